@@ -1,0 +1,203 @@
+/*
+ * dpma.h -- C ABI of the GB300 (sm_103a) Discrete Projection Moment library.
+ *
+ * The library computes every raw 3-D moment
+ *
+ *     M_pqr = sum_{x<L, y<M, z<N} V(x,y,z) x^p y^q z^r ,   p+q+r <= K        (Eq. 2)
+ *
+ * of a volume by the Discrete Projection Moment method of Diggin & Diggin,
+ * "Fast 3D Image Moments" (2020), Sec. 3:
+ *   1. project the volume into P = max(3, K+1) discrete line-sum images in one
+ *      pass over the voxels, with additions only (Sec. 3.1, Eqs. 4-9);
+ *   2. take the 2-D moments of every image (Sec. 1, Eq. 1; Sec. 3.2);
+ *   3. combine them linearly into the 3-D moments (Eqs. 10-15, generalised to
+ *      any K <= 8 by an exact integer combine matrix per degree).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * Volume layout: V[(z*M + y)*L + x], x contiguous, 0-based coordinates with
+ *   the origin at voxel (0,0,0) and 0^0 = 1 (Eq. 2).
+ * Element types: DPMA_U8 (uint8), DPMA_U16 (uint16), DPMA_F32 (float32).
+ * Moment order ("graded"): degree n = p+q+r ascending, then p descending,
+ *   then q descending: 000,100,010,001,200,110,101,020,011,002,...
+ *   dpma_num_moments(K) = (K+1)(K+2)(K+3)/6 values (20, 35, 84, 165 for
+ *   K = 3, 4, 6, 8).
+ * Moment types: integer volumes give exact signed 128-bit integers stored
+ *   little-endian in 16 bytes (low 64 bits first); float32 volumes give
+ *   IEEE doubles.
+ * Images: image k holds the sums of V along one lattice direction and is a
+ *   row-major [S_k][F_k] array; a voxel lands on row
+ *   s = slow_k(x,y,z) + off_s and column f = fast_k(x,y,z) + off_f:
+ *
+ *     k  sums along  slow        fast          S_k      F_k      paper
+ *     0  z           y           x             M        L        Eq. 5
+ *     1  x           z           y             N        M        Eq. 6
+ *     2  y           z           x             N        L        Eq. 7
+ *     3  (1,0,-1)    y           x+z           M        L+N-1    Eq. 8
+ *     4  (1,0,1)     y           x-z+(N-1)     M        L+N-1    Eq. 9
+ *     5  (1,-1,0)    z           x+y           N        L+M-1    +-pi/4 about z
+ *     6  (1,1,0)     z           x-y+(M-1)     N        L+M-1    (Sec. 3.1)
+ *     7  (0,1,-1)    y+z         x             M+N-1    L        +-pi/4 about x
+ *     8  (0,1,1)     y-z+(N-1)   x             M+N-1    L        (Sec. 3.1)
+ *
+ *   Integer volumes: uint32 pixels (exact: dimensions are capped at 65536,
+ *   so a line sum of uint16 voxels stays below 2^32).  Float32 volumes: two
+ *   float32 planes per image, the running sum and its compensation (the
+ *   pixel's value is hi + lo).
+ * 2-D moments: T_ab = sum I[s][f] (s-off_s)^a (f-off_f)^b for a+b <= K (signed
+ *   coordinates, the origin shift of Sec. 5), ordered degree ascending then
+ *   a descending; (K+1)(K+2)/2 values per image, int128 for integer volumes,
+ *   (hi, lo) float32 pairs for float volumes.
+ * Pointers: "device" pointers must come from cudaMalloc (or be otherwise
+ *   addressable by the current CUDA device); "host" pointers are ordinary
+ *   process memory (pinned memory makes the copies asynchronous and faster).
+ *   The library keeps no pointer after a call returns, except where stated.
+ * Streams: arguments named `stream` are cudaStream_t values passed as void*;
+ *   NULL means the legacy default stream.
+ * Errors: every call returns a dpma_status; nothing is thrown across the
+ *   ABI.  dpma_last_error() returns a thread-local message for the last
+ *   failing call of the calling thread.
+ * Devices: calls run on the CUDA device current in the calling thread.
+ */
+#ifndef DPMA_H
+#define DPMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dpma_status {
+  DPMA_OK = 0,
+  DPMA_ERR_INVALID_ARG = 1, /* null pointer, dimension < 1 or > 65536, K outside 0..8, bad dtype */
+  DPMA_ERR_OVERFLOW = 2,    /* an exact intermediate could exceed the int128 range */
+  DPMA_ERR_OOM = 3,         /* device memory allocation failed */
+  DPMA_ERR_CUDA = 4,        /* a CUDA runtime call failed; see dpma_last_error() */
+  DPMA_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  DPMA_ERR_REJECTED = 6,    /* the request was refused (capacity) */
+  DPMA_ERR_INTERNAL = 7     /* a self-check failed (e.g. a combine division left a remainder) */
+} dpma_status;
+
+typedef enum dpma_dtype { DPMA_U8 = 0, DPMA_U16 = 1, DPMA_F32 = 2 } dpma_dtype;
+
+#define DPMA_MAX_K 8
+#define DPMA_MAX_DIM 65536
+
+/* ---------------- helpers (host only, no GPU needed) ---------------- */
+
+/* Number of moments with p+q+r <= K, i.e. C(K+3,3); 0 if K is out of range. */
+int dpma_num_moments(int K);
+/* Number of projection images the method uses for order K: max(3, K+1). */
+int dpma_num_images(int K);
+/* Position of M_pqr in graded order; -1 if p, q or r is negative or p+q+r > 8. */
+int dpma_moment_index(int p, int q, int r);
+/* Static text for a status code. */
+const char* dpma_status_string(dpma_status s);
+/* Thread-local message describing the calling thread's last failure ("" if none). */
+const char* dpma_last_error(void);
+/* Geometry of image k (0..8) of an L x M x N volume (table above). */
+dpma_status dpma_image_geometry(int k, int64_t L, int64_t M, int64_t N, int64_t* S, int64_t* F,
+                                int64_t* off_s, int64_t* off_f);
+/* Bytes of the image buffer dpma_project writes (all P images, layout above). */
+size_t dpma_images_size(int64_t L, int64_t M, int64_t N, dpma_dtype dtype, int K);
+/* Bytes of device workspace dpma_moments_async needs (images + partial sums + status). */
+size_t dpma_workspace_size(int64_t L, int64_t M, int64_t N, dpma_dtype dtype, int K);
+/*
+ * The exact combine of degree n for order K (Sec. 3.2 generalised):
+ *   M_n = (1/D) * C * t,   t[j] = T_{a[j], n-a[j]} of image img[j],
+ * M_n being the degree-n moments in graded order.  C is nmono x nmono
+ * row-major (nmono = (n+1)(n+2)/2; capacity of C: 45*45, of img and a: 45).
+ * Any output pointer may be NULL.  Returns DPMA_ERR_INVALID_ARG unless
+ * 0 <= n <= K <= 8.
+ */
+dpma_status dpma_combine_plan(int K, int n, int* nmono, int64_t* D, int32_t* img, int32_t* a,
+                              int64_t* C);
+
+/* ---------------- the hot path ---------------- */
+
+/*
+ * All moments of a device-resident volume; synchronous.  `volume` and `out`
+ * are device pointers (out: dpma_num_moments(K) entries of 16 bytes for
+ * integer volumes, 8 bytes for float volumes).  Runs on a library-owned
+ * stream with a library-owned workspace and returns after the result is in
+ * `out`.  The library's stream is a blocking stream, so work queued on the
+ * legacy default stream (e.g. the copy that filled `volume`) completes
+ * first.  Errors: INVALID_ARG, OVERFLOW (only for integer volumes whose
+ * bound exceeds int128), OOM, CUDA, INTERNAL.
+ */
+dpma_status dpma_moments(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dtype dtype,
+                         int K, void* out);
+
+/*
+ * Same, enqueued on `stream`; returns once enqueued.  `workspace` is a
+ * device buffer of at least dpma_workspace_size(...) bytes owned by the
+ * caller (it must stay untouched until the stream has finished the call);
+ * if it is NULL the library uses its own buffer and the call serialises
+ * with other NULL-workspace calls on the same device.  A combine self-check
+ * failure is reported by the next synchronous call, not by this one.
+ */
+dpma_status dpma_moments_async(const void* volume, int64_t L, int64_t M, int64_t N,
+                               dpma_dtype dtype, int K, void* out, void* stream, void* workspace,
+                               size_t workspace_bytes);
+
+/*
+ * End to end from host memory: copies the volume host->device, computes,
+ * copies the moments device->host, and returns when `host_out` holds them.
+ * `host_volume` and `host_out` are host pointers; device buffers are owned
+ * and reused by the library.
+ */
+dpma_status dpma_moments_host(const void* host_volume, int64_t L, int64_t M, int64_t N,
+                              dpma_dtype dtype, int K, void* host_out);
+
+/*
+ * Step 1 alone (Sec. 3.1, Eqs. 4-9): writes the P = dpma_num_images(K)
+ * images of the device volume into the device buffer `images`
+ * (dpma_images_size bytes; zeroed by the call), enqueued on `stream`.
+ */
+dpma_status dpma_project(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dtype dtype,
+                         int K, void* images, void* stream);
+
+/*
+ * Step 2 alone (Eq. 1 with signed coordinates): the 2-D moments of images
+ * laid out as dpma_project writes them, into the device buffer `moments2d`
+ * (P * (K+1)(K+2)/2 values; int128 or float32 pairs), enqueued on `stream`.
+ * `workspace` as for dpma_moments_async.
+ */
+dpma_status dpma_image_moments(const void* images, int64_t L, int64_t M, int64_t N,
+                               dpma_dtype dtype, int K, void* moments2d, void* stream,
+                               void* workspace, size_t workspace_bytes);
+
+/*
+ * Step 3 alone (Eqs. 10-15 generalised): 3-D moments from the 2-D moments
+ * of dpma_image_moments (device buffers), enqueued on `stream`.  Integer
+ * combines are exact (256-bit accumulation, exact division); a division
+ * that leaves a remainder sets DPMA_ERR_INTERNAL in `status` (a device int,
+ * may be NULL).
+ */
+dpma_status dpma_combine(const void* moments2d, dpma_dtype dtype, int K, void* out, void* stream,
+                         int* status);
+
+/* ---------------- profiling aid ---------------- */
+
+/*
+ * Per-stage device timing, off by default.  While enabled, the hot-path
+ * calls record CUDA events on their launching stream around each stage:
+ * 0 = clearing the image buffer, 1 = projection (Sec. 3.1), 2 = image
+ * moments, 3 = combine.  The events add no device work.
+ */
+dpma_status dpma_stage_timing(int enable);
+/*
+ * Waits for the recorded events and returns, per stage, the summed device
+ * milliseconds (`ms[4]`) and the number of library kernels launched
+ * (`launches[4]`) since the last reset; `reset` != 0 clears the totals.
+ * Either array may be NULL.
+ */
+dpma_status dpma_stage_times(double* ms, int64_t* launches, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPMA_H */

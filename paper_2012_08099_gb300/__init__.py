@@ -1,1 +1,289 @@
-"""GB300-native Discrete Projection Moment library (placeholder, filled in below)."""
+"""GB300-native Discrete Projection Moment library (Diggin & Diggin 2020).
+
+Thin ctypes binding over ``libdpma.so`` (C ABI declared in
+``include/dpma.h``).  Every step of the computation runs in the library's
+CUDA kernels; this module only marshals arguments.  PyTorch supplies device
+memory and streams.  If the compiled library is missing, every call raises
+``RuntimeError``; there is no fallback.
+
+Volumes are tensors of shape ``(N, M, L)`` (z, y, x) with x contiguous.
+Moments come back in graded order (degree ascending, then p descending,
+then q descending): exact Python ints for integer volumes, float64 for
+float32 volumes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdpma.so")
+
+U8, U16, F32 = 0, 1, 2
+STATUS = {
+    0: "ok", 1: "invalid argument", 2: "exact range exceeded", 3: "out of device memory",
+    4: "CUDA error", 5: "device wait timed out", 6: "request rejected",
+    7: "internal self-check failed",
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class DpmaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+def lib():
+    """The loaded ``libdpma.so`` (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build it with "
+                    "`python -m paper_2012_08099_gb300.build` (needs nvcc)")
+            L = ctypes.CDLL(LIB_PATH)
+            i64, vp, ip, sz = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+            P64 = ctypes.POINTER(ctypes.c_int64)
+            sigs = {
+                "dpma_num_moments": (ip, [ip]),
+                "dpma_num_images": (ip, [ip]),
+                "dpma_moment_index": (ip, [ip, ip, ip]),
+                "dpma_status_string": (ctypes.c_char_p, [ip]),
+                "dpma_last_error": (ctypes.c_char_p, []),
+                "dpma_image_geometry": (ip, [ip, i64, i64, i64, P64, P64, P64, P64]),
+                "dpma_images_size": (sz, [i64, i64, i64, ip, ip]),
+                "dpma_workspace_size": (sz, [i64, i64, i64, ip, ip]),
+                "dpma_combine_plan": (ip, [ip, ip, ctypes.POINTER(ctypes.c_int), P64,
+                                           ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int32), P64]),
+                "dpma_moments": (ip, [vp, i64, i64, i64, ip, ip, vp]),
+                "dpma_moments_async": (ip, [vp, i64, i64, i64, ip, ip, vp, vp, vp, sz]),
+                "dpma_moments_host": (ip, [vp, i64, i64, i64, ip, ip, vp]),
+                "dpma_project": (ip, [vp, i64, i64, i64, ip, ip, vp, vp]),
+                "dpma_image_moments": (ip, [vp, i64, i64, i64, ip, ip, vp, vp, vp, sz]),
+                "dpma_combine": (ip, [vp, ip, ip, vp, vp, vp]),
+                "dpma_stage_timing": (ip, [ip]),
+                "dpma_stage_times": (ip, [ctypes.POINTER(ctypes.c_double), P64, ip]),
+            }
+            for name, (res, args) in sigs.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise DpmaError(rc, lib().dpma_last_error().decode())
+
+
+# ---------------------------------------------------------------- helpers
+
+
+def num_moments(K: int) -> int:
+    return lib().dpma_num_moments(K)
+
+
+def num_images(K: int) -> int:
+    return lib().dpma_num_images(K)
+
+
+def moment_index(p: int, q: int, r: int) -> int:
+    return lib().dpma_moment_index(p, q, r)
+
+
+def image_geometry(k: int, L: int, M: int, N: int) -> tuple[int, int, int, int]:
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(lib().dpma_image_geometry(k, L, M, N, *[ctypes.byref(x) for x in v]))
+    return tuple(int(x.value) for x in v)
+
+
+def images_size(L, M, N, dtype: int, K: int) -> int:
+    return int(lib().dpma_images_size(L, M, N, dtype, K))
+
+
+def workspace_size(L, M, N, dtype: int, K: int) -> int:
+    return int(lib().dpma_workspace_size(L, M, N, dtype, K))
+
+
+def combine_plan(K: int, n: int):
+    """(D, img, a, C) of the exact degree-n combine for order K."""
+    nm = ctypes.c_int()
+    D = ctypes.c_int64()
+    img = (ctypes.c_int32 * 45)()
+    a = (ctypes.c_int32 * 45)()
+    C = (ctypes.c_int64 * (45 * 45))()
+    _check(lib().dpma_combine_plan(K, n, ctypes.byref(nm), ctypes.byref(D), img, a, C))
+    m = nm.value
+    Cm = np.array(C[: m * m], dtype=np.int64).reshape(m, m)
+    return int(D.value), list(img[:m]), list(a[:m]), Cm
+
+
+def int128_to_ints(words) -> list[int]:
+    """Little-endian int128 values given as (lo, hi) int64 pairs -> Python ints."""
+    w = np.asarray(words, dtype=np.int64).reshape(-1, 2)
+    return [((int(hi) << 64) | (int(lo) & 0xFFFFFFFFFFFFFFFF)) for lo, hi in w]
+
+
+def dtype_code(t) -> int:
+    """Library dtype of a torch tensor or numpy array (uint16 may arrive as int16 bits)."""
+    name = str(getattr(t, "dtype", t)).replace("torch.", "")
+    if name == "uint8":
+        return U8
+    if name in ("uint16",):
+        return U16
+    if name == "float32":
+        return F32
+    raise TypeError(f"unsupported volume dtype {name}; use uint8, uint16 or float32")
+
+
+def _shape(vol):
+    if vol.dim() != 3:
+        raise ValueError("volume must be 3-D (N, M, L)")
+    if not vol.is_contiguous():
+        raise ValueError("volume must be contiguous (x fastest)")
+    N, M, L = vol.shape
+    return int(L), int(M), int(N)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+# ------------------------------------------------------------- hot path
+
+
+def moments(volume, K: int, dtype: int | None = None, out=None):
+    """All moments M_pqr, p+q+r <= K, of a CUDA volume (synchronous).
+
+    ``volume``: CUDA tensor (N, M, L); pass ``dtype=U16`` when uint16 data
+    is held in an int16 tensor.  Returns exact ints or a float64 tensor.
+    """
+    import torch
+    dt = dtype_code(volume) if dtype is None else dtype
+    L, M, N = _shape(volume)
+    nm = lib().dpma_num_moments(K)
+    if nm == 0:
+        raise DpmaError(1, "K must lie in 0..8")
+    if out is None:
+        out = torch.empty((nm, 2) if dt != F32 else (nm,),
+                          dtype=torch.int64 if dt != F32 else torch.float64, device=volume.device)
+    with torch.cuda.device(volume.device):
+        _check(lib().dpma_moments(ctypes.c_void_p(volume.data_ptr()), L, M, N, dt, K,
+                                  ctypes.c_void_p(out.data_ptr())))
+    return out
+
+
+def moments_values(volume, K: int, dtype: int | None = None):
+    """Like :func:`moments` but returns host values (ints or float64 numpy)."""
+    dt = dtype_code(volume) if dtype is None else dtype
+    out = moments(volume, K, dt)
+    if dt == F32:
+        return out.cpu().numpy()
+    return int128_to_ints(out.cpu().numpy())
+
+
+def moments_async(volume, K: int, out, dtype: int | None = None, stream=None, workspace=None):
+    """Enqueue the three steps on ``stream`` (default: torch's current stream)."""
+    dt = dtype_code(volume) if dtype is None else dtype
+    L, M, N = _shape(volume)
+    ws_ptr = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else None
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().dpma_moments_async(ctypes.c_void_p(volume.data_ptr()), L, M, N, dt, K,
+                                    ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream),
+                                    ws_ptr, ws_bytes))
+    return out
+
+
+def moments_host(volume: np.ndarray, K: int, dtype: int | None = None, out: np.ndarray | None = None):
+    """End to end from host memory (copies in, computes, copies out)."""
+    vol = np.ascontiguousarray(volume)
+    dt = dtype_code(vol) if dtype is None else dtype
+    N, M, L = vol.shape
+    nm = lib().dpma_num_moments(K)
+    if out is None:
+        out = np.empty((nm, 2) if dt != F32 else (nm,), dtype=np.int64 if dt != F32 else np.float64)
+    _check(lib().dpma_moments_host(ctypes.c_void_p(vol.ctypes.data), L, M, N, dt, K,
+                                   ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def project(volume, K: int, dtype: int | None = None, stream=None):
+    """Step 1 alone: the projection images as a list of CPU numpy arrays.
+
+    Integer volumes give uint64 arrays [S_k, F_k]; float volumes give float64
+    arrays holding hi + lo.
+    """
+    import torch
+    dt = dtype_code(volume) if dtype is None else dtype
+    L, M, N = _shape(volume)
+    nbytes = images_size(L, M, N, dt, K)
+    buf = torch.empty(nbytes // 4, dtype=torch.int32, device=volume.device)
+    _check(lib().dpma_project(ctypes.c_void_p(volume.data_ptr()), L, M, N, dt, K,
+                              ctypes.c_void_p(buf.data_ptr()), _stream_ptr(stream)))
+    torch.cuda.synchronize(volume.device)
+    host = buf.cpu().numpy()
+    imgs, at = [], 0
+    for k in range(num_images(K)):
+        S, F, _, _ = image_geometry(k, L, M, N)
+        if dt == F32:
+            f = host.view(np.float32)
+            hi = f[at:at + S * F].astype(np.float64)
+            lo = f[at + S * F:at + 2 * S * F].astype(np.float64)
+            imgs.append((hi + lo).reshape(S, F))
+            at += 2 * S * F
+        else:
+            imgs.append(host.view(np.uint32)[at:at + S * F].astype(np.uint64).reshape(S, F))
+            at += S * F
+    return imgs
+
+
+def image_moments_of(volume, K: int, dtype: int | None = None):
+    """Steps 1+2 through the C ABI: per-image 2-D moments (ints or float64)."""
+    import torch
+    dt = dtype_code(volume) if dtype is None else dtype
+    L, M, N = _shape(volume)
+    P = num_images(K)
+    npairs = (K + 1) * (K + 2) // 2
+    imgs = torch.empty(images_size(L, M, N, dt, K) // 4, dtype=torch.int32, device=volume.device)
+    st = _stream_ptr(None)
+    _check(lib().dpma_project(ctypes.c_void_p(volume.data_ptr()), L, M, N, dt, K,
+                              ctypes.c_void_p(imgs.data_ptr()), st))
+    m2d = torch.empty(P * npairs * (2 if dt == F32 else 4), dtype=torch.int32,
+                      device=volume.device)
+    _check(lib().dpma_image_moments(ctypes.c_void_p(imgs.data_ptr()), L, M, N, dt, K,
+                                    ctypes.c_void_p(m2d.data_ptr()), st, None, 0))
+    torch.cuda.synchronize(volume.device)
+    h = m2d.cpu().numpy()
+    if dt == F32:
+        f = h.view(np.float32).reshape(P, npairs, 2).astype(np.float64)
+        return f[:, :, 0] + f[:, :, 1]
+    vals = int128_to_ints(h.view(np.int64))
+    return [vals[k * npairs:(k + 1) * npairs] for k in range(P)]
+
+
+# ------------------------------------------------------------ profiling
+
+
+def stage_timing(enable: bool) -> None:
+    """Record CUDA events around each stage of the hot-path calls."""
+    _check(lib().dpma_stage_timing(1 if enable else 0))
+
+
+def stage_times(reset: bool = True):
+    """(ms[4], launches[4]) per stage: 0 clear, 1 projection, 2 image moments, 3 combine."""
+    ms = (ctypes.c_double * 4)()
+    n = (ctypes.c_int64 * 4)()
+    _check(lib().dpma_stage_times(ms, n, 1 if reset else 0))
+    return list(ms), list(n)

@@ -1,0 +1,452 @@
+// C ABI of the Discrete Projection Moment library (declared in include/dpma.h).
+//
+// Host-side argument checks, magnitude bounds, workspace layout and stream
+// handling around the three device steps:
+//   step 1  launch_project        (Sec. 3.1, Eqs. 4-9)
+//   step 2  launch_image_moments  (Eq. 1 with signed coordinates)
+//   step 3  launch_combine        (Eqs. 10-15 generalised)
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/dpma.h"
+#include "dpma_internal.cuh"
+
+namespace dpma {
+cudaError_t prepare_combine(int K);
+}
+
+using namespace dpma;
+
+namespace {
+
+thread_local std::string t_last_error;
+
+dpma_status fail(dpma_status s, const std::string& msg) {
+  t_last_error = msg;
+  return s;
+}
+
+dpma_status cuda_fail(cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(DPMA_ERR_OOM, std::string(where) + ": " + cudaGetErrorString(e));
+  }
+  return fail(DPMA_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+bool is_float(dpma_dtype d) { return d == DPMA_F32; }
+
+dpma_status check_args(int64_t L, int64_t M, int64_t N, dpma_dtype dtype, int K) {
+  if (L < 1 || M < 1 || N < 1 || L > DPMA_MAX_DIM || M > DPMA_MAX_DIM || N > DPMA_MAX_DIM)
+    return fail(DPMA_ERR_INVALID_ARG, "dimensions must lie in 1..65536");
+  if (K < 0 || K > DPMA_MAX_K) return fail(DPMA_ERR_INVALID_ARG, "K must lie in 0..8");
+  if (dtype != DPMA_U8 && dtype != DPMA_U16 && dtype != DPMA_F32)
+    return fail(DPMA_ERR_INVALID_ARG, "unknown dtype");
+  if (dtype == DPMA_F32) {
+    // float-float coordinate powers must stay well inside the float range
+    const double maxc = (double)(L + M + N);
+    if (K * std::log2(maxc) > 100.0)
+      return fail(DPMA_ERR_OVERFLOW, "coordinate powers exceed the float32 range");
+  } else {
+    const double vmax = dtype == DPMA_U8 ? 255.0 : 65535.0;
+    if (log2_bound_2d(L, M, N, vmax, K) > 125.0 || log2_bound_3d(L, M, N, vmax, K) > 125.0)
+      return fail(DPMA_ERR_OVERFLOW, "moments could exceed the int128 range");
+  }
+  return DPMA_OK;
+}
+
+struct Layout {
+  ImageSet set;
+  size_t img_bytes, part_bytes, m2d_bytes;
+  size_t off_img, off_part, off_m2d, off_status, total;
+};
+
+Layout layout(int64_t L, int64_t M, int64_t N, dpma_dtype dtype, int K) {
+  Layout w;
+  const bool fl = is_float(dtype);
+  w.set = make_image_set(L, M, N, K, fl);
+  w.img_bytes = (size_t)w.set.total_elems * 4;
+  w.part_bytes = moments2d_partials_bytes(w.set, K, fl);
+  w.m2d_bytes = (size_t)w.set.P * num_2d(K) * (fl ? 8 : 16);
+  w.off_img = 0;
+  w.off_part = align_up(w.off_img + w.img_bytes, 256);
+  w.off_m2d = align_up(w.off_part + w.part_bytes, 256);
+  w.off_status = align_up(w.off_m2d + w.m2d_bytes, 256);
+  w.total = w.off_status + 256;
+  return w;
+}
+
+// Library-owned per-device resources.
+struct DeviceState {
+  std::mutex mu;
+  cudaStream_t stream = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  void* host_vol = nullptr;  // device buffers of dpma_moments_host
+  size_t host_vol_bytes = 0;
+  void* host_out = nullptr;
+};
+
+std::mutex g_states_mu;
+std::unordered_map<int, DeviceState*> g_states;
+
+DeviceState* state_for_current_device(int* dev_out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  if (dev_out) *dev_out = dev;
+  std::lock_guard<std::mutex> lk(g_states_mu);
+  auto it = g_states.find(dev);
+  if (it != g_states.end()) return it->second;
+  DeviceState* s = new DeviceState();
+  g_states[dev] = s;
+  return s;
+}
+
+cudaError_t ensure_stream(DeviceState* s) {
+  if (s->stream) return cudaSuccess;
+  // a blocking stream: it waits for work queued on the legacy default stream
+  return cudaStreamCreateWithFlags(&s->stream, cudaStreamDefault);
+}
+
+cudaError_t ensure_buffer(void** p, size_t* have, size_t need) {
+  if (*have >= need && *p) return cudaSuccess;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  cudaError_t e = cudaMalloc(p, need);
+  if (e == cudaSuccess) *have = need;
+  return e;
+}
+
+// Optional per-stage event timing (profiling aid, off by default).
+struct StageEvent {
+  int stage;
+  cudaEvent_t a, b;
+};
+std::mutex g_timing_mu;
+bool g_timing = false;
+std::vector<StageEvent> g_pending;
+std::vector<cudaEvent_t> g_free_events;
+double g_stage_ms[4] = {0, 0, 0, 0};
+int64_t g_stage_launches[4] = {0, 0, 0, 0};
+// kernel launches each stage makes (memsets are not kernels of this library)
+constexpr int kStageKernels[4] = {0, 1, 2, 1};
+
+cudaEvent_t take_event() {
+  if (!g_free_events.empty()) {
+    cudaEvent_t e = g_free_events.back();
+    g_free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct StageRecorder {
+  bool on;
+  cudaStream_t st;
+  cudaEvent_t last = nullptr;
+  explicit StageRecorder(cudaStream_t s) : st(s) {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    on = g_timing;
+    if (on) { last = take_event(); cudaEventRecord(last, st); }
+  }
+  void mark(int stage) {
+    if (!on) return;
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    cudaEvent_t e = take_event();
+    cudaEventRecord(e, st);
+    g_pending.push_back({stage, last, e});
+    last = take_event();
+    cudaEventRecord(last, st);
+  }
+  ~StageRecorder() {
+    if (!on) return;
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    g_free_events.push_back(last);
+  }
+};
+
+// Enqueue the three steps on `st` with workspace `ws` (layout `w`).
+dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dtype dtype, int K,
+                    void* out, cudaStream_t st, unsigned char* ws, const Layout& w) {
+  cudaError_t e = prepare_combine(K);
+  if (e != cudaSuccess) return cuda_fail(e, "combine plan");
+  StageRecorder rec(st);
+  void* images = ws + w.off_img;
+  e = cudaMemsetAsync(images, 0, w.img_bytes, st);
+  if (e != cudaSuccess) return cuda_fail(e, "clear images");
+  e = cudaMemsetAsync(ws + w.off_status, 0, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "clear status");
+  rec.mark(0);
+  ProjectArgs a;
+  a.vol = volume;
+  a.L = L; a.M = M; a.N = N;
+  a.dtype = (int)dtype;
+  a.K = K;
+  a.images = images;
+  a.set = w.set;
+  e = launch_project(a, st);
+  if (e != cudaSuccess) return cuda_fail(e, "projection kernel");
+  rec.mark(1);
+  const bool fl = is_float(dtype);
+  e = launch_image_moments(images, w.set, K, fl, ws + w.off_part, ws + w.off_m2d, st);
+  if (e != cudaSuccess) return cuda_fail(e, "image moment kernel");
+  rec.mark(2);
+  e = launch_combine(ws + w.off_m2d, K, fl, out, reinterpret_cast<int*>(ws + w.off_status), st);
+  if (e != cudaSuccess) return cuda_fail(e, "combine kernel");
+  rec.mark(3);
+  return DPMA_OK;
+}
+
+size_t elem_size(dpma_dtype d) { return d == DPMA_U8 ? 1 : (d == DPMA_U16 ? 2 : 4); }
+
+}  // namespace
+
+extern "C" {
+
+int dpma_num_moments(int K) { return (K < 0 || K > DPMA_MAX_K) ? 0 : num_moments(K); }
+
+int dpma_num_images(int K) { return (K < 0 || K > DPMA_MAX_K) ? 0 : num_images(K); }
+
+int dpma_moment_index(int p, int q, int r) {
+  if (p < 0 || q < 0 || r < 0 || p + q + r > DPMA_MAX_K) return -1;
+  return idx3d(p, q, r);
+}
+
+const char* dpma_status_string(dpma_status s) {
+  switch (s) {
+    case DPMA_OK: return "ok";
+    case DPMA_ERR_INVALID_ARG: return "invalid argument";
+    case DPMA_ERR_OVERFLOW: return "exact range exceeded";
+    case DPMA_ERR_OOM: return "out of device memory";
+    case DPMA_ERR_CUDA: return "CUDA error";
+    case DPMA_ERR_TIMEOUT: return "device wait timed out";
+    case DPMA_ERR_REJECTED: return "request rejected";
+    case DPMA_ERR_INTERNAL: return "internal self-check failed";
+  }
+  return "unknown status";
+}
+
+const char* dpma_last_error(void) { return t_last_error.c_str(); }
+
+dpma_status dpma_image_geometry(int k, int64_t L, int64_t M, int64_t N, int64_t* S, int64_t* F,
+                                int64_t* off_s, int64_t* off_f) {
+  if (k < 0 || k >= kMaxImages || L < 1 || M < 1 || N < 1)
+    return fail(DPMA_ERR_INVALID_ARG, "bad image index or dimensions");
+  ImageGeom g;
+  image_geom(k, L, M, N, &g);
+  if (S) *S = g.S;
+  if (F) *F = g.F;
+  if (off_s) *off_s = g.off_s;
+  if (off_f) *off_f = g.off_f;
+  return DPMA_OK;
+}
+
+size_t dpma_images_size(int64_t L, int64_t M, int64_t N, dpma_dtype dtype, int K) {
+  if (check_args(L, M, N, dtype, K) == DPMA_ERR_INVALID_ARG) return 0;
+  return layout(L, M, N, dtype, K).img_bytes;
+}
+
+size_t dpma_workspace_size(int64_t L, int64_t M, int64_t N, dpma_dtype dtype, int K) {
+  if (check_args(L, M, N, dtype, K) == DPMA_ERR_INVALID_ARG) return 0;
+  return layout(L, M, N, dtype, K).total;
+}
+
+dpma_status dpma_combine_plan(int K, int n, int* nmono, int64_t* D, int32_t* img, int32_t* a,
+                              int64_t* C) {
+  if (K < 0 || K > DPMA_MAX_K || n < 0 || n > K)
+    return fail(DPMA_ERR_INVALID_ARG, "need 0 <= n <= K <= 8");
+  const CombinePlan* cp = combine_plan(K);
+  if (!cp) return fail(DPMA_ERR_INTERNAL, "combine plan failed its exact check");
+  const DegreePlan& d = cp->deg[n];
+  if (nmono) *nmono = d.nmono;
+  if (D) *D = d.D;
+  for (int j = 0; j < d.nmono; ++j) {
+    if (img) img[j] = d.img[j];
+    if (a) a[j] = d.a[j];
+  }
+  if (C) std::memcpy(C, d.C, sizeof(int64_t) * d.nmono * d.nmono);
+  return DPMA_OK;
+}
+
+dpma_status dpma_moments_async(const void* volume, int64_t L, int64_t M, int64_t N,
+                               dpma_dtype dtype, int K, void* out, void* stream, void* workspace,
+                               size_t workspace_bytes) {
+  if (!volume || !out) return fail(DPMA_ERR_INVALID_ARG, "null volume or output pointer");
+  dpma_status s = check_args(L, M, N, dtype, K);
+  if (s != DPMA_OK) return s;
+  const Layout w = layout(L, M, N, dtype, K);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (workspace) {
+    if (workspace_bytes < w.total) return fail(DPMA_ERR_INVALID_ARG, "workspace too small");
+    return enqueue(volume, L, M, N, dtype, K, out, st, static_cast<unsigned char*>(workspace), w);
+  }
+  DeviceState* ds = state_for_current_device(nullptr);
+  if (!ds) return fail(DPMA_ERR_CUDA, "no current CUDA device");
+  std::lock_guard<std::mutex> lk(ds->mu);
+  cudaError_t e = ensure_buffer(&ds->ws, &ds->ws_bytes, w.total);
+  if (e != cudaSuccess) return cuda_fail(e, "workspace");
+  return enqueue(volume, L, M, N, dtype, K, out, st, static_cast<unsigned char*>(ds->ws), w);
+}
+
+dpma_status dpma_moments(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dtype dtype,
+                         int K, void* out) {
+  if (!volume || !out) return fail(DPMA_ERR_INVALID_ARG, "null volume or output pointer");
+  dpma_status s = check_args(L, M, N, dtype, K);
+  if (s != DPMA_OK) return s;
+  DeviceState* ds = state_for_current_device(nullptr);
+  if (!ds) return fail(DPMA_ERR_CUDA, "no current CUDA device");
+  std::lock_guard<std::mutex> lk(ds->mu);
+  cudaError_t e = ensure_stream(ds);
+  if (e != cudaSuccess) return cuda_fail(e, "stream");
+  const Layout w = layout(L, M, N, dtype, K);
+  e = ensure_buffer(&ds->ws, &ds->ws_bytes, w.total);
+  if (e != cudaSuccess) return cuda_fail(e, "workspace");
+  unsigned char* ws = static_cast<unsigned char*>(ds->ws);
+  s = enqueue(volume, L, M, N, dtype, K, out, ds->stream, ws, w);
+  if (s != DPMA_OK) return s;
+  int status = 0;
+  e = cudaMemcpyAsync(&status, ws + w.off_status, sizeof(int), cudaMemcpyDeviceToHost, ds->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ds->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+  if (status) return fail(DPMA_ERR_INTERNAL, "combine division left a remainder");
+  return DPMA_OK;
+}
+
+dpma_status dpma_moments_host(const void* host_volume, int64_t L, int64_t M, int64_t N,
+                              dpma_dtype dtype, int K, void* host_out) {
+  if (!host_volume || !host_out) return fail(DPMA_ERR_INVALID_ARG, "null host pointer");
+  dpma_status s = check_args(L, M, N, dtype, K);
+  if (s != DPMA_OK) return s;
+  DeviceState* ds = state_for_current_device(nullptr);
+  if (!ds) return fail(DPMA_ERR_CUDA, "no current CUDA device");
+  std::lock_guard<std::mutex> lk(ds->mu);
+  cudaError_t e = ensure_stream(ds);
+  if (e != cudaSuccess) return cuda_fail(e, "stream");
+  const Layout w = layout(L, M, N, dtype, K);
+  const size_t vbytes = (size_t)L * M * N * elem_size(dtype);
+  const size_t obytes = (size_t)num_moments(DPMA_MAX_K) * 16;
+  // one allocation: [volume | moments] so the workspace can stay separate
+  size_t need = align_up(vbytes, 256) + obytes;
+  e = ensure_buffer(&ds->host_vol, &ds->host_vol_bytes, need);
+  if (e != cudaSuccess) return cuda_fail(e, "staging buffer");
+  ds->host_out = static_cast<unsigned char*>(ds->host_vol) + align_up(vbytes, 256);
+  e = ensure_buffer(&ds->ws, &ds->ws_bytes, w.total);
+  if (e != cudaSuccess) return cuda_fail(e, "workspace");
+  e = cudaMemcpyAsync(ds->host_vol, host_volume, vbytes, cudaMemcpyHostToDevice, ds->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copy volume to device");
+  unsigned char* ws = static_cast<unsigned char*>(ds->ws);
+  s = enqueue(ds->host_vol, L, M, N, dtype, K, ds->host_out, ds->stream, ws, w);
+  if (s != DPMA_OK) return s;
+  const size_t out_bytes = (size_t)num_moments(K) * (is_float(dtype) ? 8 : 16);
+  int status = 0;
+  e = cudaMemcpyAsync(host_out, ds->host_out, out_bytes, cudaMemcpyDeviceToHost, ds->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&status, ws + w.off_status, sizeof(int), cudaMemcpyDeviceToHost, ds->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ds->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copy moments to host");
+  if (status) return fail(DPMA_ERR_INTERNAL, "combine division left a remainder");
+  return DPMA_OK;
+}
+
+dpma_status dpma_project(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dtype dtype,
+                         int K, void* images, void* stream) {
+  if (!volume || !images) return fail(DPMA_ERR_INVALID_ARG, "null volume or image pointer");
+  dpma_status s = check_args(L, M, N, dtype, K);
+  if (s != DPMA_OK && s != DPMA_ERR_OVERFLOW) return s;  // images alone are always exact
+  const Layout w = layout(L, M, N, dtype, K);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(images, 0, w.img_bytes, st);
+  if (e != cudaSuccess) return cuda_fail(e, "clear images");
+  ProjectArgs a;
+  a.vol = volume;
+  a.L = L; a.M = M; a.N = N;
+  a.dtype = (int)dtype;
+  a.K = K;
+  a.images = images;
+  a.set = w.set;
+  e = launch_project(a, st);
+  if (e != cudaSuccess) return cuda_fail(e, "projection kernel");
+  return DPMA_OK;
+}
+
+dpma_status dpma_image_moments(const void* images, int64_t L, int64_t M, int64_t N,
+                               dpma_dtype dtype, int K, void* moments2d, void* stream,
+                               void* workspace, size_t workspace_bytes) {
+  if (!images || !moments2d) return fail(DPMA_ERR_INVALID_ARG, "null image or output pointer");
+  dpma_status s = check_args(L, M, N, dtype, K);
+  if (s != DPMA_OK) return s;
+  const Layout w = layout(L, M, N, dtype, K);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* part = nullptr;
+  if (workspace) {
+    if (workspace_bytes < w.total) return fail(DPMA_ERR_INVALID_ARG, "workspace too small");
+    part = static_cast<unsigned char*>(workspace) + w.off_part;
+    cudaError_t e = launch_image_moments(images, w.set, K, is_float(dtype), part, moments2d, st);
+    if (e != cudaSuccess) return cuda_fail(e, "image moment kernel");
+    return DPMA_OK;
+  }
+  DeviceState* ds = state_for_current_device(nullptr);
+  if (!ds) return fail(DPMA_ERR_CUDA, "no current CUDA device");
+  std::lock_guard<std::mutex> lk(ds->mu);
+  cudaError_t e = ensure_buffer(&ds->ws, &ds->ws_bytes, w.total);
+  if (e != cudaSuccess) return cuda_fail(e, "workspace");
+  part = static_cast<unsigned char*>(ds->ws) + w.off_part;
+  e = launch_image_moments(images, w.set, K, is_float(dtype), part, moments2d, st);
+  if (e != cudaSuccess) return cuda_fail(e, "image moment kernel");
+  return DPMA_OK;
+}
+
+dpma_status dpma_combine(const void* moments2d, dpma_dtype dtype, int K, void* out, void* stream,
+                         int* status) {
+  if (!moments2d || !out) return fail(DPMA_ERR_INVALID_ARG, "null pointer");
+  if (K < 0 || K > DPMA_MAX_K) return fail(DPMA_ERR_INVALID_ARG, "K must lie in 0..8");
+  if (dtype != DPMA_U8 && dtype != DPMA_U16 && dtype != DPMA_F32)
+    return fail(DPMA_ERR_INVALID_ARG, "unknown dtype");
+  cudaError_t e = prepare_combine(K);
+  if (e != cudaSuccess) return cuda_fail(e, "combine plan");
+  e = launch_combine(moments2d, K, is_float(dtype), out, status, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "combine kernel");
+  return DPMA_OK;
+}
+
+dpma_status dpma_stage_timing(int enable) {
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  g_timing = enable != 0;
+  return DPMA_OK;
+}
+
+dpma_status dpma_stage_times(double* ms, int64_t* launches, int reset) {
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  for (const StageEvent& se : g_pending) {
+    cudaError_t e = cudaEventSynchronize(se.b);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, se.a, se.b);
+    if (e != cudaSuccess) {
+      g_pending.clear();
+      return cuda_fail(e, "stage timing events");
+    }
+    g_stage_ms[se.stage] += t;
+    g_stage_launches[se.stage] += kStageKernels[se.stage];
+    g_free_events.push_back(se.a);
+    g_free_events.push_back(se.b);
+  }
+  g_pending.clear();
+  for (int i = 0; i < 4; ++i) {
+    if (ms) ms[i] = g_stage_ms[i];
+    if (launches) launches[i] = g_stage_launches[i];
+    if (reset) { g_stage_ms[i] = 0; g_stage_launches[i] = 0; }
+  }
+  return DPMA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// Internal declarations shared by the kernels and the C ABI of the Discrete
+// Projection Moment library (Diggin & Diggin 2020, Sec. 3).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "plan.h"
+
+namespace dpma {
+
+using i128 = __int128;
+using u128 = unsigned __int128;
+
+// Geometry of the P images of one volume, packed for kernels.
+struct ImageSet {
+  int P;
+  int64_t S[kMaxImages], F[kMaxImages];
+  int64_t off_s[kMaxImages], off_f[kMaxImages];
+  // element offset of image k inside the image buffer (uint32 pixels for
+  // integer volumes; for float volumes the hi plane starts here and the lo
+  // plane follows it at + S*F)
+  int64_t base[kMaxImages];
+  int64_t total_elems;  // uint32 elements (int) or float elements (both planes)
+};
+
+inline ImageSet make_image_set(int64_t L, int64_t M, int64_t N, int K, bool is_float) {
+  ImageSet s{};
+  s.P = num_images(K);
+  int64_t at = 0;
+  for (int k = 0; k < s.P; ++k) {
+    ImageGeom g;
+    image_geom(k, L, M, N, &g);
+    s.S[k] = g.S; s.F[k] = g.F; s.off_s[k] = g.off_s; s.off_f[k] = g.off_f;
+    s.base[k] = at;
+    at += g.S * g.F * (is_float ? 2 : 1);
+  }
+  s.total_elems = at;
+  return s;
+}
+
+// ---------------- float-float helpers (error-free transformations) ----------
+
+// s + e == a + b exactly (Knuth's TwoSum, 6 flops, no ordering condition).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// p + e == a * b exactly (fused multiply-add based TwoProd).
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+
+// (hi, lo) += (bh, bl), renormalised.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float bh, float bl) {
+  float s, e;
+  two_sum(hi, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(lo, bl));
+  hi = __fadd_rn(s, e);
+  lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+// ---------------- kernel launchers (defined in the .cu files) ----------------
+
+struct ProjectArgs {
+  const void* vol;
+  int64_t L, M, N;
+  int dtype;  // 0 u8, 1 u16, 2 f32
+  int K;
+  void* images;
+  ImageSet set;
+};
+
+// Step 1: images must be zeroed by the caller (the launcher does not clear).
+cudaError_t launch_project(const ProjectArgs& a, cudaStream_t st);
+
+// Step 2: block partials of every image's 2-D moments into `partials`
+// (int128 or float pairs), then a reduction into `m2d`.
+size_t moments2d_partials_bytes(const ImageSet& set, int K, bool is_float);
+cudaError_t launch_image_moments(const void* images, const ImageSet& set, int K, bool is_float,
+                                 void* partials, void* m2d, cudaStream_t st);
+
+// Step 3: combine into 3-D moments.
+cudaError_t launch_combine(const void* m2d, int K, bool is_float, void* out, int* status,
+                           cudaStream_t st);
+
+}  // namespace dpma

@@ -1,0 +1,255 @@
+// Step 2 of the Discrete Projection Moment method: the 2-D moments of every
+// projection image (Sec. 1, Eq. 1; Sec. 3.2), with signed coordinates so
+// the origin shift of the negative-index images (Sec. 5) is built in:
+//
+//     T_ab = sum_s (s - off_s)^a * F_b(s),   F_b(s) = sum_f I[s][f] (f - off_f)^b.
+//
+// The paper obtains the same values from 1-D Discrete Radon integrals of
+// each image (its DRT listing); on a GPU the separable power sums above are
+// cheaper and exact, and they give identical results.
+//
+// One warp handles one image row at a time: lanes stride over the row and
+// accumulate F_b for b = 0..K, a butterfly reduction gives every lane the
+// row totals, and lane t then adds (s - off_s)^a F_b for the (a, b) pairs
+// it owns.  A CTA covers kRowsPerBlock rows of one image and writes one
+// partial vector per image pair; the combine kernel sums the partials.
+// Integer images accumulate exactly in int128; float images accumulate in
+// float-float (pairs of float32), so no FP64 arithmetic happens here.
+#include <cstdint>
+
+#include "dpma_internal.cuh"
+
+namespace dpma {
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr int kRowsPerBlock = 64;
+
+struct K2Params {
+  const void* images;
+  ImageSet set;
+  int K;
+  int npairs;
+  int64_t blk_base[kMaxImages + 1];  // first block of each image; [P] = total
+  void* partials;                    // [block][npairs] int128 or float2
+};
+
+__device__ __forceinline__ i128 shfl_xor_i128(i128 v, int m) {
+  unsigned long long lo = (unsigned long long)(u128)v;
+  unsigned long long hi = (unsigned long long)((u128)v >> 64);
+  lo = __shfl_xor_sync(0xffffffffu, lo, m);
+  hi = __shfl_xor_sync(0xffffffffu, hi, m);
+  return (i128)(((u128)hi << 64) | lo);
+}
+
+__global__ void __launch_bounds__(kThreads) k2_int_kernel(K2Params p) {
+  const int blk = blockIdx.x;
+  int k = 0;
+  while (k + 1 < p.set.P && blk >= p.blk_base[k + 1]) ++k;
+  const int64_t chunk = blk - p.blk_base[k];
+  const int64_t S = p.set.S[k], F = p.set.F[k];
+  const int64_t off_s = p.set.off_s[k], off_f = p.set.off_f[k];
+  const uint32_t* img = static_cast<const uint32_t*>(p.images) + p.set.base[k];
+  const int K = p.K;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // pairs owned by this lane: index lane and lane + 32
+  int pa[2], pb[2];
+  for (int t = 0; t < 2; ++t) {
+    int idx = lane + 32 * t;
+    pa[t] = -1; pb[t] = -1;
+    if (idx < p.npairs) {
+      int n = 0;
+      while ((n + 1) * (n + 2) / 2 <= idx) ++n;
+      int a = n - (idx - n * (n + 1) / 2);
+      pa[t] = a; pb[t] = n - a;
+    }
+  }
+  i128 T[2] = {0, 0};
+
+  const int64_t r0 = chunk * kRowsPerBlock;
+  const int64_t r1 = (r0 + kRowsPerBlock < S) ? r0 + kRowsPerBlock : S;
+  for (int64_t s = r0 + warp; s < r1; s += kWarps) {
+    i128 Fb[kMaxK + 1];
+#pragma unroll
+    for (int b = 0; b <= kMaxK; ++b) Fb[b] = 0;
+    const uint32_t* row = img + s * F;
+    for (int64_t f = lane; f < F; f += 32) {
+      const uint32_t v = row[f];
+      if (!v) continue;
+      const int64_t c = f - off_f;
+      i128 t = (i128)v;
+#pragma unroll
+      for (int b = 0; b <= kMaxK; ++b) {
+        if (b > K) break;
+        Fb[b] += t;
+        t *= (i128)c;
+      }
+    }
+#pragma unroll
+    for (int b = 0; b <= kMaxK; ++b) {
+      if (b > K) break;
+#pragma unroll
+      for (int m = 16; m >= 1; m >>= 1) Fb[b] += shfl_xor_i128(Fb[b], m);
+    }
+    const i128 cs = (i128)(s - off_s);
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      if (pa[t] < 0) continue;
+      i128 w = 1;
+      for (int e = 0; e < pa[t]; ++e) w *= cs;
+      i128 fb = 0;
+#pragma unroll
+      for (int b = 0; b <= kMaxK; ++b)
+        if (b == pb[t]) fb = Fb[b];
+      T[t] += w * fb;
+    }
+  }
+
+  // reduce the kWarps partial vectors of this CTA
+  __shared__ i128 red[kWarps][64];
+  red[warp][lane] = T[0];
+  red[warp][lane + 32] = T[1];
+  __syncthreads();
+  if (warp == 0) {
+    for (int t = 0; t < 2; ++t) {
+      const int idx = lane + 32 * t;
+      if (idx >= p.npairs) continue;
+      i128 acc = 0;
+      for (int w = 0; w < kWarps; ++w) acc += red[w][idx];
+      static_cast<i128*>(p.partials)[(int64_t)blk * p.npairs + idx] = acc;
+    }
+  }
+}
+
+// float-float helpers -------------------------------------------------------
+
+// (hi, lo) * c for a float c whose products stay finite.
+__device__ __forceinline__ void ff_mul_f(float hi, float lo, float c, float& rh, float& rl) {
+  float p, e;
+  two_prod(hi, c, p, e);
+  e = __fmaf_rn(lo, c, e);
+  rh = __fadd_rn(p, e);
+  rl = __fsub_rn(e, __fsub_rn(rh, p));
+}
+
+__global__ void __launch_bounds__(kThreads) k2_f32_kernel(K2Params p) {
+  const int blk = blockIdx.x;
+  int k = 0;
+  while (k + 1 < p.set.P && blk >= p.blk_base[k + 1]) ++k;
+  const int64_t chunk = blk - p.blk_base[k];
+  const int64_t S = p.set.S[k], F = p.set.F[k];
+  const int64_t off_s = p.set.off_s[k], off_f = p.set.off_f[k];
+  const float* hi_plane = static_cast<const float*>(p.images) + p.set.base[k];
+  const float* lo_plane = hi_plane + S * F;
+  const int K = p.K;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  int pa[2], pb[2];
+  for (int t = 0; t < 2; ++t) {
+    int idx = lane + 32 * t;
+    pa[t] = -1; pb[t] = -1;
+    if (idx < p.npairs) {
+      int n = 0;
+      while ((n + 1) * (n + 2) / 2 <= idx) ++n;
+      int a = n - (idx - n * (n + 1) / 2);
+      pa[t] = a; pb[t] = n - a;
+    }
+  }
+  float Th[2] = {0.f, 0.f}, Tl[2] = {0.f, 0.f};
+
+  const int64_t r0 = chunk * kRowsPerBlock;
+  const int64_t r1 = (r0 + kRowsPerBlock < S) ? r0 + kRowsPerBlock : S;
+  for (int64_t s = r0 + warp; s < r1; s += kWarps) {
+    float Fh[kMaxK + 1], Fl[kMaxK + 1];
+#pragma unroll
+    for (int b = 0; b <= kMaxK; ++b) { Fh[b] = 0.f; Fl[b] = 0.f; }
+    const float* rh = hi_plane + s * F;
+    const float* rl = lo_plane + s * F;
+    for (int64_t f = lane; f < F; f += 32) {
+      float th = rh[f], tl = rl[f];
+      if (th == 0.f && tl == 0.f) continue;
+      const float c = (float)(f - off_f);
+#pragma unroll
+      for (int b = 0; b <= kMaxK; ++b) {
+        if (b > K) break;
+        ff_add(Fh[b], Fl[b], th, tl);
+        ff_mul_f(th, tl, c, th, tl);
+      }
+    }
+#pragma unroll
+    for (int b = 0; b <= kMaxK; ++b) {
+      if (b > K) break;
+#pragma unroll
+      for (int m = 16; m >= 1; m >>= 1) {
+        float oh = __shfl_xor_sync(0xffffffffu, Fh[b], m);
+        float ol = __shfl_xor_sync(0xffffffffu, Fl[b], m);
+        ff_add(Fh[b], Fl[b], oh, ol);
+      }
+    }
+    const float cs = (float)(s - off_s);
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      if (pa[t] < 0) continue;
+      float fh = 0.f, fl = 0.f;
+#pragma unroll
+      for (int b = 0; b <= kMaxK; ++b)
+        if (b == pb[t]) { fh = Fh[b]; fl = Fl[b]; }
+      for (int e = 0; e < pa[t]; ++e) ff_mul_f(fh, fl, cs, fh, fl);
+      ff_add(Th[t], Tl[t], fh, fl);
+    }
+  }
+
+  __shared__ float2 red[kWarps][64];
+  red[warp][lane] = make_float2(Th[0], Tl[0]);
+  red[warp][lane + 32] = make_float2(Th[1], Tl[1]);
+  __syncthreads();
+  if (warp == 0) {
+    for (int t = 0; t < 2; ++t) {
+      const int idx = lane + 32 * t;
+      if (idx >= p.npairs) continue;
+      float ah = 0.f, al = 0.f;
+      for (int w = 0; w < kWarps; ++w) ff_add(ah, al, red[w][idx].x, red[w][idx].y);
+      static_cast<float2*>(p.partials)[(int64_t)blk * p.npairs + idx] = make_float2(ah, al);
+    }
+  }
+}
+
+int64_t blocks_of(const ImageSet& set, int64_t* base) {
+  int64_t at = 0;
+  for (int k = 0; k < set.P; ++k) {
+    if (base) base[k] = at;
+    at += (set.S[k] + kRowsPerBlock - 1) / kRowsPerBlock;
+  }
+  if (base) base[set.P] = at;
+  return at;
+}
+
+}  // namespace
+
+size_t moments2d_partials_bytes(const ImageSet& set, int K, bool is_float) {
+  return (size_t)blocks_of(set, nullptr) * num_2d(K) * (is_float ? sizeof(float2) : sizeof(i128));
+}
+
+// defined in k3_combine.cu: sums the block partials into per-image moments
+cudaError_t launch_reduce_partials(const void* partials, const int64_t* blk_base, int P, int K,
+                                   bool is_float, void* m2d, cudaStream_t st);
+
+cudaError_t launch_image_moments(const void* images, const ImageSet& set, int K, bool is_float,
+                                 void* partials, void* m2d, cudaStream_t st) {
+  K2Params p;
+  p.images = images;
+  p.set = set;
+  p.K = K;
+  p.npairs = num_2d(K);
+  const int64_t nblk = blocks_of(set, p.blk_base);
+  p.partials = partials;
+  if (is_float) k2_f32_kernel<<<(unsigned)nblk, kThreads, 0, st>>>(p);
+  else k2_int_kernel<<<(unsigned)nblk, kThreads, 0, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_reduce_partials(partials, p.blk_base, set.P, K, is_float, m2d, st);
+}
+
+}  // namespace dpma

@@ -1,0 +1,263 @@
+// Step 3 of the Discrete Projection Moment method: the 3-D moments from the
+// 2-D moments of the projection images (Sec. 3.2, Eqs. 10-15, generalised to
+// every degree n <= K with an exact integer combine per degree).
+//
+// Integer volumes: the 2-D moments are exact int128 values; each 3-D moment
+// is  (sum_j C[m][j] T_j) / D  with the sum accumulated in 256-bit two's
+// complement and divided exactly (a non-zero remainder means the images
+// were not those of any volume and is reported as a self-check failure).
+// Float volumes: the float-float 2-D moments are widened to FP64 here, the
+// only FP64 arithmetic of the pipeline, because the combine cancels terms.
+#include <cstdint>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "dpma_internal.cuh"
+
+namespace dpma {
+namespace {
+
+constexpr int kStatusInternal = 7;
+
+// ---------------- partial reduction ----------------
+
+struct RedParams {
+  const void* partials;
+  int64_t blk_base[kMaxImages + 1];
+  int P, npairs;
+  void* m2d;
+};
+
+__global__ void reduce_int_kernel(RedParams p) {
+  const int k = blockIdx.x;
+  const int t = threadIdx.x;
+  if (t >= p.npairs) return;
+  const i128* part = static_cast<const i128*>(p.partials);
+  i128 acc = 0;
+  for (int64_t b = p.blk_base[k]; b < p.blk_base[k + 1]; ++b) acc += part[b * p.npairs + t];
+  static_cast<i128*>(p.m2d)[k * p.npairs + t] = acc;
+}
+
+__global__ void reduce_f32_kernel(RedParams p) {
+  const int k = blockIdx.x;
+  const int t = threadIdx.x;
+  if (t >= p.npairs) return;
+  const float2* part = static_cast<const float2*>(p.partials);
+  float h = 0.f, l = 0.f;
+  for (int64_t b = p.blk_base[k]; b < p.blk_base[k + 1]; ++b) {
+    float2 v = part[b * p.npairs + t];
+    ff_add(h, l, v.x, v.y);
+  }
+  static_cast<float2*>(p.m2d)[k * p.npairs + t] = make_float2(h, l);
+}
+
+// ---------------- 256-bit helpers ----------------
+
+struct I256 {
+  uint64_t w[4];
+};
+
+__device__ __forceinline__ void neg256(I256& a) {
+  uint64_t carry = 1;
+  for (int i = 0; i < 4; ++i) {
+    uint64_t v = ~a.w[i] + carry;
+    carry = (carry && v == 0) ? 1 : 0;
+    a.w[i] = v;
+  }
+}
+
+__device__ __forceinline__ void add256(I256& a, const I256& b) {
+  unsigned long long carry = 0;
+  for (int i = 0; i < 4; ++i) {
+    u128 s = (u128)a.w[i] + b.w[i] + carry;
+    a.w[i] = (uint64_t)s;
+    carry = (unsigned long long)(s >> 64);
+  }
+}
+
+// a += c * t   (c: int64, t: int128)
+__device__ __forceinline__ void mac256(I256& a, int64_t c, i128 t) {
+  if (c == 0 || t == 0) return;
+  const bool neg = (c < 0) != (t < 0);
+  const uint64_t uc = c < 0 ? (uint64_t)(-(c + 1)) + 1 : (uint64_t)c;
+  const u128 ut = t < 0 ? (u128)(-(t + 1)) + 1 : (u128)t;
+  const u128 p0 = (u128)uc * (uint64_t)ut;
+  const u128 p1 = (u128)uc * (uint64_t)(ut >> 64);
+  const u128 mid = (p0 >> 64) + (u128)(uint64_t)p1;
+  I256 prod;
+  prod.w[0] = (uint64_t)p0;
+  prod.w[1] = (uint64_t)mid;
+  prod.w[2] = (uint64_t)(p1 >> 64) + (uint64_t)(mid >> 64);
+  prod.w[3] = 0;
+  if (neg) neg256(prod);
+  add256(a, prod);
+}
+
+// q = a / d exactly; returns false on a remainder or if q leaves int128.
+__device__ bool div256_exact(I256 a, int64_t d, i128* q) {
+  const bool neg = (a.w[3] >> 63) != 0;
+  if (neg) neg256(a);
+  uint64_t qw[4];
+  u128 rem = 0;
+  for (int i = 3; i >= 0; --i) {
+    const u128 cur = (rem << 64) | a.w[i];
+    qw[i] = (uint64_t)(cur / (uint64_t)d);
+    rem = cur % (uint64_t)d;
+  }
+  if (rem != 0) return false;
+  if (qw[3] != 0 || qw[2] != 0) return false;
+  const u128 mag = ((u128)qw[1] << 64) | qw[0];
+  if (!neg && (mag >> 127)) return false;
+  if (neg && mag > ((u128)1 << 127)) return false;
+  *q = neg ? (i128)(~mag + 1) : (i128)mag;
+  return true;
+}
+
+// ---------------- combine ----------------
+
+// Packed plan (int64 words): for n = 0..K at word off[n]:
+//   D, nmono, img[nmono], a[nmono], C[nmono * nmono]
+struct CombParams {
+  const int64_t* plan;
+  int off[kMaxK + 1];
+  int K, npairs;
+  const void* m2d;
+  void* out;
+  int* status;
+};
+
+__global__ void combine_int_kernel(CombParams p) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nmom = (p.K + 1) * (p.K + 2) * (p.K + 3) / 6;
+  if (m >= nmom) return;
+  int n = 0;
+  while ((n + 1) * (n + 2) * (n + 3) / 6 <= m) ++n;
+  const int row = m - n * (n + 1) * (n + 2) / 6;
+  const int64_t* pl = p.plan + p.off[n];
+  const int64_t D = pl[0];
+  const int nm = (int)pl[1];
+  const int64_t* img = pl + 2;
+  const int64_t* aa = img + nm;
+  const int64_t* C = aa + nm;
+  const i128* T = static_cast<const i128*>(p.m2d);
+  I256 acc = {{0, 0, 0, 0}};
+  for (int j = 0; j < nm; ++j) {
+    const int a = (int)aa[j];
+    const int b = n - a;
+    const int pair = (a + b) * (a + b + 1) / 2 + (n - a);
+    mac256(acc, C[row * nm + j], T[img[j] * p.npairs + pair]);
+  }
+  i128 q = 0;
+  if (!div256_exact(acc, D, &q)) {
+    if (p.status) atomicMax(p.status, kStatusInternal);
+    q = 0;
+  }
+  static_cast<i128*>(p.out)[m] = q;
+}
+
+__global__ void combine_f32_kernel(CombParams p) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nmom = (p.K + 1) * (p.K + 2) * (p.K + 3) / 6;
+  if (m >= nmom) return;
+  int n = 0;
+  while ((n + 1) * (n + 2) * (n + 3) / 6 <= m) ++n;
+  const int row = m - n * (n + 1) * (n + 2) / 6;
+  const int64_t* pl = p.plan + p.off[n];
+  const double D = (double)pl[0];
+  const int nm = (int)pl[1];
+  const int64_t* img = pl + 2;
+  const int64_t* aa = img + nm;
+  const int64_t* C = aa + nm;
+  const float2* T = static_cast<const float2*>(p.m2d);
+  double acc = 0.0;
+  for (int j = 0; j < nm; ++j) {
+    const int a = (int)aa[j];
+    const int pair = n * (n + 1) / 2 + (n - a);
+    const float2 t = T[img[j] * p.npairs + pair];
+    acc += (double)C[row * nm + j] * ((double)t.x + (double)t.y);
+  }
+  static_cast<double*>(p.out)[m] = acc / D;
+}
+
+struct DevPlan {
+  int64_t* words;
+  int off[kMaxK + 1];
+};
+
+std::mutex g_mu;
+std::unordered_map<int64_t, DevPlan> g_dev_plans;  // key: device * 16 + K
+
+cudaError_t device_plan(int K, DevPlan* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const int64_t key = (int64_t)dev * 16 + K;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_dev_plans.find(key);
+  if (it != g_dev_plans.end()) { *out = it->second; return cudaSuccess; }
+  const CombinePlan* cp = combine_plan(K);
+  if (!cp) return cudaErrorInvalidValue;
+  std::vector<int64_t> w;
+  DevPlan dp{};
+  for (int n = 0; n <= K; ++n) {
+    const DegreePlan& d = cp->deg[n];
+    dp.off[n] = (int)w.size();
+    w.push_back(d.D);
+    w.push_back(d.nmono);
+    for (int j = 0; j < d.nmono; ++j) w.push_back(d.img[j]);
+    for (int j = 0; j < d.nmono; ++j) w.push_back(d.a[j]);
+    for (int j = 0; j < d.nmono * d.nmono; ++j) w.push_back(d.C[j]);
+  }
+  e = cudaMalloc(&dp.words, w.size() * sizeof(int64_t));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(dp.words, w.data(), w.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { cudaFree(dp.words); return e; }
+  g_dev_plans[key] = dp;
+  *out = dp;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_reduce_partials(const void* partials, const int64_t* blk_base, int P, int K,
+                                   bool is_float, void* m2d, cudaStream_t st) {
+  RedParams p;
+  p.partials = partials;
+  for (int k = 0; k <= P; ++k) p.blk_base[k] = blk_base[k];
+  p.P = P;
+  p.npairs = num_2d(K);
+  if (is_float) reduce_f32_kernel<<<P, 64, 0, st>>>(p);
+  else reduce_int_kernel<<<P, 64, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+// Ensures the plan of order K is resident on the current device (host call,
+// synchronous the first time).
+cudaError_t prepare_combine(int K) {
+  DevPlan dp{};
+  return device_plan(K, &dp);
+}
+
+cudaError_t launch_combine(const void* m2d, int K, bool is_float, void* out, int* status,
+                           cudaStream_t st) {
+  DevPlan dp{};
+  cudaError_t e = device_plan(K, &dp);
+  if (e != cudaSuccess) return e;
+  CombParams p;
+  p.plan = dp.words;
+  for (int n = 0; n <= kMaxK; ++n) p.off[n] = dp.off[n];
+  p.K = K;
+  p.npairs = num_2d(K);
+  p.m2d = m2d;
+  p.out = out;
+  p.status = status;
+  const int nmom = num_moments(K);
+  const int threads = 64;
+  const int blocks = (nmom + threads - 1) / threads;
+  if (is_float) combine_f32_kernel<<<blocks, threads, 0, st>>>(p);
+  else combine_int_kernel<<<blocks, threads, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace dpma

@@ -1,0 +1,173 @@
+"""C-ABI checks that need no GPU.
+
+* the library loads and exports every function ``include/dpma.h`` declares;
+* host-only helpers (moment order, image geometry, buffer sizes) agree with
+  the oracle's independent definitions;
+* the exact combine plan: C A_sel = D I recomputed here in Python integers
+  from the image forms, full rank with K+1 directions, the denominators of
+  every degree, and -- applied in Python to the oracle's 2-D moments -- it
+  reproduces the oracle's 3-D moments exactly (the paper's Eqs. 10-15 are
+  the K <= 4 special case);
+* argument validation of host-only calls.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2012_08099_gb300 as dpma
+from paper_2012_08099_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+FORMS = {
+    0: ((0, 1, 0), (1, 0, 0)), 1: ((0, 0, 1), (0, 1, 0)), 2: ((0, 0, 1), (1, 0, 0)),
+    3: ((0, 1, 0), (1, 0, 1)), 4: ((0, 1, 0), (1, 0, -1)), 5: ((0, 0, 1), (1, 1, 0)),
+    6: ((0, 0, 1), (1, -1, 0)), 7: ((0, 1, 1), (1, 0, 0)), 8: ((0, 1, -1), (1, 0, 0)),
+}
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(dpma.LIB_PATH):
+        from paper_2012_08099_gb300 import build
+        build.build()
+    return dpma.lib()
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "dpma.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(dpma_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_moment_order_matches_oracle(lib):
+    for K in range(9):
+        assert dpma.num_moments(K) == oracle.num_moments(K)
+        assert dpma.num_images(K) == oracle.num_images(K)
+        for i, (p, q, r) in enumerate(oracle.graded_triples(K)):
+            assert dpma.moment_index(p, q, r) == i
+    assert dpma.num_moments(9) == 0 and dpma.num_moments(-1) == 0
+    assert dpma.moment_index(5, 4, 0) == -1 and dpma.moment_index(-1, 0, 0) == -1
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (7, 5, 3), (64, 64, 64), (512, 300, 17)])
+def test_image_geometry_matches_oracle(lib, dims):
+    L, M, N = dims
+    for k in range(9):
+        assert dpma.image_geometry(k, L, M, N) == oracle.image_geometry(k, L, M, N)
+
+
+def test_buffer_sizes(lib):
+    L, M, N = 37, 21, 13
+    for dt, per in ((dpma.U8, 4), (dpma.U16, 4), (dpma.F32, 8)):
+        for K in (0, 3, 6, 8):
+            want = sum(oracle.image_geometry(k, L, M, N)[0] * oracle.image_geometry(k, L, M, N)[1]
+                       for k in range(oracle.num_images(K))) * per
+            assert dpma.images_size(L, M, N, dt, K) == want
+            assert dpma.workspace_size(L, M, N, dt, K) > want
+    assert dpma.images_size(0, 5, 5, dpma.U8, 3) == 0
+    assert dpma.workspace_size(5, 5, 5, dpma.U8, 9) == 0
+
+
+def expand(fs, ff, a, b, n):
+    """Row of (fs.x)^a (ff.x)^b over the degree-n monomials in graded order."""
+    poly = {(0, 0, 0): 1}
+    for form in [fs] * a + [ff] * b:
+        nxt = {}
+        for e, c in poly.items():
+            for d, w in enumerate(form):
+                if w:
+                    e2 = list(e)
+                    e2[d] += 1
+                    nxt[tuple(e2)] = nxt.get(tuple(e2), 0) + c * w
+        poly = nxt
+    monos = [(p, q, n - p - q) for p in range(n, -1, -1) for q in range(n - p, -1, -1)]
+    return [poly.get(m, 0) for m in monos]
+
+
+@pytest.mark.parametrize("K", [0, 1, 2, 3, 4, 5, 6, 7, 8])
+def test_combine_plan_is_an_exact_inverse(lib, K):
+    for n in range(K + 1):
+        D, img, a, C = dpma.combine_plan(K, n)
+        nm = (n + 1) * (n + 2) // 2
+        assert C.shape == (nm, nm)
+        assert all(0 <= i < dpma.num_images(K) for i in img)
+        A = np.array([expand(*FORMS[i], aa, n - aa, n) for i, aa in zip(img, a)], dtype=object)
+        prod = np.array(C, dtype=object).dot(A)
+        assert (prod == D * np.eye(nm, dtype=object)).all()
+
+
+def test_combine_denominators():
+    # D_n per degree, independent of K once enough images exist
+    want = [1, 1, 1, 2, 6, 24, 120, 120, 1680]
+    for n in range(9):
+        assert dpma.combine_plan(8, n)[0] == want[n]
+    assert max(abs(int(v)) for n in range(9) for v in dpma.combine_plan(8, n)[3].ravel()) == 4200
+
+
+def test_k_plus_one_directions_are_needed():
+    """With K directions the degree-K system is rank deficient (so P = K+1)."""
+    from fractions import Fraction
+
+    def rank(rows):
+        m = [[Fraction(v) for v in r] for r in rows]
+        rk, col = 0, 0
+        ncol = len(m[0])
+        while rk < len(m) and col < ncol:
+            piv = next((i for i in range(rk, len(m)) if m[i][col] != 0), None)
+            if piv is None:
+                col += 1
+                continue
+            m[rk], m[piv] = m[piv], m[rk]
+            for i in range(len(m)):
+                if i != rk and m[i][col] != 0:
+                    f = m[i][col] / m[rk][col]
+                    m[i] = [x - f * y for x, y in zip(m[i], m[rk])]
+            rk += 1
+            col += 1
+        return rk
+
+    for n in (3, 4, 6):
+        nm = (n + 1) * (n + 2) // 2
+        full = [expand(*FORMS[k], a, n - a, n) for k in range(n + 1) for a in range(n, -1, -1)]
+        short = [expand(*FORMS[k], a, n - a, n) for k in range(n) for a in range(n, -1, -1)]
+        assert rank(full) == nm
+        assert rank(short) < nm
+
+
+@pytest.mark.parametrize("K,dtype", [(3, np.uint8), (4, np.uint16), (6, np.uint16), (8, np.uint8)])
+def test_plan_applied_to_oracle_image_moments_gives_oracle_moments(K, dtype):
+    vol = synth.uniform_volume((5, 6, 7), dtype, seed=K)
+    N, M, L = vol.shape
+    imgs = oracle.project(vol, oracle.num_images(K))
+    T = []
+    for k, im in enumerate(imgs):
+        S, F, os_, of = oracle.image_geometry(k, L, M, N)
+        T.append(oracle.image_moments(im, os_, of, K))
+    m3 = oracle.moments(vol, K)
+    for n in range(K + 1):
+        D, img, a, C = dpma.combine_plan(K, n)
+        t = [T[i][n * (n + 1) // 2 + (n - aa)] for i, aa in zip(img, a)]
+        for row in range(C.shape[0]):
+            acc = sum(int(c) * v for c, v in zip(C[row], t))
+            assert acc % D == 0
+            m = n * (n + 1) * (n + 2) // 6 + row
+            assert acc // D == m3[m]
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert lib.dpma_status_string(s)
+    assert lib.dpma_combine_plan(3, 4, None, None, None, None, None) == 1
+    assert b"0 <= n <= K" in lib.dpma_last_error()
