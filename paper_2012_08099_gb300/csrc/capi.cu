@@ -187,7 +187,7 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
   e = cudaMemsetAsync(ws + w.off_status, 0, sizeof(int), st);
   if (e != cudaSuccess) return cuda_fail(e, "clear status");
   rec.mark(0);
-  ProjectArgs a;
+  ProjectArgs a{};
   a.vol = volume;
   a.L = L; a.M = M; a.N = N;
   a.dtype = (int)dtype;
@@ -367,7 +367,7 @@ dpma_status dpma_project(const void* volume, int64_t L, int64_t M, int64_t N, dp
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(images, 0, w.img_bytes, st);
   if (e != cudaSuccess) return cuda_fail(e, "clear images");
-  ProjectArgs a;
+  ProjectArgs a{};
   a.vol = volume;
   a.L = L; a.M = M; a.N = N;
   a.dtype = (int)dtype;

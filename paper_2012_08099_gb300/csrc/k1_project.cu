@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p) {
 template <typename T, int P>
 cudaError_t launch_t(const ProjectArgs& a, cudaStream_t st) {
   constexpr bool FL = std::is_same<T, float>::value;
-  K1Params p;
+  K1Params p{};
   p.vol = a.vol;
   p.L = a.L; p.M = a.M; p.N = a.N;
   p.nbands = (a.M + BY - 1) / BY;

@@ -238,7 +238,7 @@ cudaError_t launch_reduce_partials(const void* partials, const int64_t* blk_base
 
 cudaError_t launch_image_moments(const void* images, const ImageSet& set, int K, bool is_float,
                                  void* partials, void* m2d, cudaStream_t st) {
-  K2Params p;
+  K2Params p{};
   p.images = images;
   p.set = set;
   p.K = K;

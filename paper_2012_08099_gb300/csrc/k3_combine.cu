@@ -222,8 +222,9 @@ cudaError_t device_plan(int K, DevPlan* out) {
 
 cudaError_t launch_reduce_partials(const void* partials, const int64_t* blk_base, int P, int K,
                                    bool is_float, void* m2d, cudaStream_t st) {
-  RedParams p;
+  RedParams p{};
   p.partials = partials;
+  p.m2d = m2d;
   for (int k = 0; k <= P; ++k) p.blk_base[k] = blk_base[k];
   p.P = P;
   p.npairs = num_2d(K);
@@ -244,7 +245,7 @@ cudaError_t launch_combine(const void* m2d, int K, bool is_float, void* out, int
   DevPlan dp{};
   cudaError_t e = device_plan(K, &dp);
   if (e != cudaSuccess) return e;
-  CombParams p;
+  CombParams p{};
   p.plan = dp.words;
   for (int n = 0; n <= kMaxK; ++n) p.off[n] = dp.off[n];
   p.K = K;
