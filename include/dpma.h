@@ -35,10 +35,10 @@
  *     2  y           z           x             N        L        Eq. 7
  *     3  (1,0,-1)    y           x+z           M        L+N-1    Eq. 8
  *     4  (1,0,1)     y           x-z+(N-1)     M        L+N-1    Eq. 9
- *     5  (1,-1,0)    z           x+y           N        L+M-1    +-pi/4 about z
- *     6  (1,1,0)     z           x-y+(M-1)     N        L+M-1    (Sec. 3.1)
- *     7  (0,1,-1)    y+z         x             M+N-1    L        +-pi/4 about x
- *     8  (0,1,1)     y-z+(N-1)   x             M+N-1    L        (Sec. 3.1)
+ *     5  (0,1,-1)    y+z         x             M+N-1    L        +-pi/4 about x
+ *     6  (0,1,1)     y-z+(N-1)   x             M+N-1    L        (Sec. 3.1)
+ *     7  (1,-1,0)    z           x+y           N        L+M-1    +-pi/4 about z
+ *     8  (1,1,0)     z           x-y+(M-1)     N        L+M-1    (Sec. 3.1)
  *
  *   Integer volumes: uint32 pixels (exact: dimensions are capped at 65536,
  *   so a line sum of uint16 voxels stays below 2^32).  Float32 volumes: two

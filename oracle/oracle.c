@@ -35,13 +35,13 @@
  *   2  y                z                 x                 N        L
  *   3  (1,0,-1)         y                 x+z               M        L+N-1
  *   4  (1,0,1)          y                 x-z+(N-1)         M        L+N-1
- *   5  (1,-1,0)         z                 x+y               N        L+M-1
- *   6  (1,1,0)          z                 x-y+(M-1)         N        L+M-1
- *   7  (0,1,-1)         y+z               x                 M+N-1    L
- *   8  (0,1,1)          y-z+(N-1)         x                 M+N-1    L
+ *   5  (0,1,-1)         y+z               x                 M+N-1    L
+ *   6  (0,1,1)          y-z+(N-1)         x                 M+N-1    L
+ *   7  (1,-1,0)         z                 x+y               N        L+M-1
+ *   8  (1,1,0)          z                 x-y+(M-1)         N        L+M-1
  *
  * Images 0-2 are Eqs. 5-7, images 3-4 are Eqs. 8-9 and images 5-8 are the
- * remaining +-pi/4 projections about the z and x axes.  The signed
+ * remaining +-pi/4 projections about the x and z axes (Sec. 3.1).  The signed
  * coordinate of an offset column or row is the stored index minus the
  * offset (the origin shift described in Sec. 5).
  */
@@ -286,10 +286,10 @@ int oracle_image_geometry(int k, int64_t L, int64_t M, int64_t N, int64_t* S, in
         case 2: s = N; f = L; break;
         case 3: s = M; f = L + N - 1; break;
         case 4: s = M; f = L + N - 1; of = N - 1; break;
-        case 5: s = N; f = L + M - 1; break;
-        case 6: s = N; f = L + M - 1; of = M - 1; break;
-        case 7: s = M + N - 1; f = L; break;
-        case 8: s = M + N - 1; f = L; os = N - 1; break;
+        case 5: s = M + N - 1; f = L; break;
+        case 6: s = M + N - 1; f = L; os = N - 1; break;
+        case 7: s = N; f = L + M - 1; break;
+        case 8: s = N; f = L + M - 1; of = M - 1; break;
         default: return 1;
     }
     *S = s; *F = f; *off_s = os; *off_f = of;
@@ -304,10 +304,10 @@ static void image_coords(int k, int64_t x, int64_t y, int64_t z, int64_t* s, int
         case 2: *s = z;     *f = x;     break;
         case 3: *s = y;     *f = x + z; break;
         case 4: *s = y;     *f = x - z; break;
-        case 5: *s = z;     *f = x + y; break;
-        case 6: *s = z;     *f = x - y; break;
-        case 7: *s = y + z; *f = x;     break;
-        default: *s = y - z; *f = x;    break;
+        case 5: *s = y + z; *f = x;     break;
+        case 6: *s = y - z; *f = x;     break;
+        case 7: *s = z;     *f = x + y; break;
+        default: *s = z;    *f = x - y; break;
     }
 }
 

@@ -194,6 +194,7 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
   a.K = K;
   a.images = images;
   a.set = w.set;
+  a.status = reinterpret_cast<int*>(ws + w.off_status);
   e = launch_project(a, st);
   if (e != cudaSuccess) return cuda_fail(e, "projection kernel");
   rec.mark(1);
@@ -318,6 +319,7 @@ dpma_status dpma_moments(const void* volume, int64_t L, int64_t M, int64_t N, dp
   e = cudaMemcpyAsync(&status, ws + w.off_status, sizeof(int), cudaMemcpyDeviceToHost, ds->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ds->stream);
   if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+  if (status == DPMA_ERR_TIMEOUT) return fail(DPMA_ERR_TIMEOUT, "a bounded device wait gave up");
   if (status) return fail(DPMA_ERR_INTERNAL, "combine division left a remainder");
   return DPMA_OK;
 }
@@ -354,6 +356,7 @@ dpma_status dpma_moments_host(const void* host_volume, int64_t L, int64_t M, int
     e = cudaMemcpyAsync(&status, ws + w.off_status, sizeof(int), cudaMemcpyDeviceToHost, ds->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ds->stream);
   if (e != cudaSuccess) return cuda_fail(e, "copy moments to host");
+  if (status == DPMA_ERR_TIMEOUT) return fail(DPMA_ERR_TIMEOUT, "a bounded device wait gave up");
   if (status) return fail(DPMA_ERR_INTERNAL, "combine division left a remainder");
   return DPMA_OK;
 }

@@ -71,6 +71,7 @@ struct ProjectArgs {
   int K;
   void* images;
   ImageSet set;
+  int* status;  // device status word for bounded-wait timeouts (may be null)
 };
 
 // Step 1: images must be zeroed by the caller (the launcher does not clear).

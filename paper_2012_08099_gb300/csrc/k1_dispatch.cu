@@ -1,0 +1,27 @@
+// Step 1 dispatch: element type and image count -> kernel instantiation.
+// The instantiations live in k1_inst_*.cu so they compile in parallel.
+#include "dpma_internal.cuh"
+
+namespace dpma {
+namespace k1 {
+cudaError_t launch_u8_lo(int P, const ProjectArgs& a, cudaStream_t st);
+cudaError_t launch_u8_hi(int P, const ProjectArgs& a, cudaStream_t st);
+cudaError_t launch_u16_lo(int P, const ProjectArgs& a, cudaStream_t st);
+cudaError_t launch_u16_hi(int P, const ProjectArgs& a, cudaStream_t st);
+cudaError_t launch_f32_lo(int P, const ProjectArgs& a, cudaStream_t st);
+cudaError_t launch_f32_hi(int P, const ProjectArgs& a, cudaStream_t st);
+}  // namespace k1
+
+cudaError_t launch_project(const ProjectArgs& a, cudaStream_t st) {
+  const int P = a.set.P;
+  if (P < 3 || P > 9) return cudaErrorInvalidValue;
+  const bool hi = P >= 6;
+  switch (a.dtype) {
+    case 0: return hi ? k1::launch_u8_hi(P, a, st) : k1::launch_u8_lo(P, a, st);
+    case 1: return hi ? k1::launch_u16_hi(P, a, st) : k1::launch_u16_lo(P, a, st);
+    case 2: return hi ? k1::launch_f32_hi(P, a, st) : k1::launch_f32_lo(P, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace dpma

@@ -219,10 +219,10 @@ bool image_geom(int k, int64_t L, int64_t M, int64_t N, ImageGeom* g) {
       {{0, 0, 1}, {1, 0, 0}},   // 2: (z, x), line along y          Eq. 7
       {{0, 1, 0}, {1, 0, 1}},   // 3: (x+z, y)                      Eq. 8
       {{0, 1, 0}, {1, 0, -1}},  // 4: (x-z, y)                      Eq. 9
-      {{0, 0, 1}, {1, 1, 0}},   // 5: (x+y, z)   +-pi/4 about z
-      {{0, 0, 1}, {1, -1, 0}},  // 6: (x-y, z)
-      {{0, 1, 1}, {1, 0, 0}},   // 7: (y+z, x)   +-pi/4 about x
-      {{0, 1, -1}, {1, 0, 0}},  // 8: (y-z, x)
+      {{0, 1, 1}, {1, 0, 0}},   // 5: (y+z, x)   +-pi/4 about x
+      {{0, 1, -1}, {1, 0, 0}},  // 6: (y-z, x)
+      {{0, 0, 1}, {1, 1, 0}},   // 7: (x+y, z)   +-pi/4 about z
+      {{0, 0, 1}, {1, -1, 0}},  // 8: (x-y, z)
   };
   if (k < 0 || k >= kMaxImages) return false;
   std::memcpy(g->slow, forms[k][0], sizeof(g->slow));

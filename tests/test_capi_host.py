@@ -25,8 +25,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 FORMS = {
     0: ((0, 1, 0), (1, 0, 0)), 1: ((0, 0, 1), (0, 1, 0)), 2: ((0, 0, 1), (1, 0, 0)),
-    3: ((0, 1, 0), (1, 0, 1)), 4: ((0, 1, 0), (1, 0, -1)), 5: ((0, 0, 1), (1, 1, 0)),
-    6: ((0, 0, 1), (1, -1, 0)), 7: ((0, 1, 1), (1, 0, 0)), 8: ((0, 1, -1), (1, 0, 0)),
+    3: ((0, 1, 0), (1, 0, 1)), 4: ((0, 1, 0), (1, 0, -1)), 5: ((0, 1, 1), (1, 0, 0)),
+    6: ((0, 1, -1), (1, 0, 0)), 7: ((0, 0, 1), (1, 1, 0)), 8: ((0, 0, 1), (1, -1, 0)),
 }
 
 
@@ -109,11 +109,16 @@ def test_combine_plan_is_an_exact_inverse(lib, K):
 
 
 def test_combine_denominators():
-    # D_n per degree, independent of K once enough images exist
+    # D_n per degree (the lcm of the exact inverse's denominators); they do
+    # not depend on K once the degree has enough images
     want = [1, 1, 1, 2, 6, 24, 120, 120, 1680]
     for n in range(9):
         assert dpma.combine_plan(8, n)[0] == want[n]
-    assert max(abs(int(v)) for n in range(9) for v in dpma.combine_plan(8, n)[3].ravel()) == 4200
+        if n <= 6:
+            assert dpma.combine_plan(6, n)[0] == want[n]
+    # small integer matrices: |C| <= 2100 at K = 8, 120 at K = 6
+    assert max(abs(int(v)) for n in range(9) for v in dpma.combine_plan(8, n)[3].ravel()) == 2100
+    assert max(abs(int(v)) for n in range(7) for v in dpma.combine_plan(6, n)[3].ravel()) == 120
 
 
 def test_k_plus_one_directions_are_needed():

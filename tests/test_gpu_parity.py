@@ -7,11 +7,11 @@ Float32 volumes must satisfy, per moment,
 
 (the oracle's moment of the absolute volume), and per image pixel
 
-    |I_gpu - I_oracle| <= 64 * 2^-24 * I_oracle(|V|)
+    |I_gpu - I_oracle| <= 2^-40 * I_oracle(|V|)
 
-which is the design's worst-case bound for its short uncompensated runs
-(at most R + TY + #partials plain float additions per pixel; every longer
-accumulation is compensated).
+because every float addition of the projection is compensated (Kahan pairs
+and error-free TwoSum merges), so an image pixel carries float-float
+accuracy; a single plain float32 rounding per pixel (2^-24) would fail it.
 """
 import numpy as np
 import pytest
@@ -24,7 +24,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 FLOAT_MOMENT_TOL = 1e-6
-FLOAT_PIXEL_TOL = 64 * 2.0 ** -24
+FLOAT_PIXEL_TOL = 2.0 ** -40
 
 
 @pytest.fixture(scope="module")
@@ -162,7 +162,12 @@ def test_host_path_matches_device_path(dpma):
         K = 4
         host = dpma.moments_host(vol.view(np.int16) if dtype == np.uint16 else vol, K, dt)
         d = dpma.moments(t, K, dt).cpu().numpy()
-        np.testing.assert_array_equal(host, d)
+        if dtype == np.float32:
+            # float atomics merge partial sums in a run-dependent order
+            mag = oracle.moments(vol, K, absolute=True)
+            assert np.all(np.abs(host - d) <= 1e-12 * mag)
+        else:
+            np.testing.assert_array_equal(host, d)
 
 
 def test_repeat_calls_identical_for_integers(dpma):

@@ -26,10 +26,10 @@ FORMS = {
     2: ((0, 0, 1), (1, 0, 0)),
     3: ((0, 1, 0), (1, 0, 1)),
     4: ((0, 1, 0), (1, 0, -1)),
-    5: ((0, 0, 1), (1, 1, 0)),
-    6: ((0, 0, 1), (1, -1, 0)),
-    7: ((0, 1, 1), (1, 0, 0)),
-    8: ((0, 1, -1), (1, 0, 0)),
+    5: ((0, 1, 1), (1, 0, 0)),
+    6: ((0, 1, -1), (1, 0, 0)),
+    7: ((0, 0, 1), (1, 1, 0)),
+    8: ((0, 0, 1), (1, -1, 0)),
 }
 
 
@@ -46,8 +46,8 @@ def test_image_sizes():
     want = {
         0: (M, L), 1: (N, M), 2: (N, L),          # Eqs. 5-7 (x-y image is L x M)
         3: (M, L + N - 1), 4: (M, L + N - 1),     # Eqs. 8-9: (L+N-1) x M
-        5: (N, L + M - 1), 6: (N, L + M - 1),
-        7: (M + N - 1, L), 8: (M + N - 1, L),
+        5: (M + N - 1, L), 6: (M + N - 1, L),
+        7: (N, L + M - 1), 8: (N, L + M - 1),
     }
     for k, (S, F) in want.items():
         assert oracle.image_geometry(k, L, M, N)[:2] == (S, F)
