@@ -41,9 +41,9 @@
  *     8  (1,1,0)     z           x-y+(M-1)     N        L+M-1    (Sec. 3.1)
  *
  *   Integer volumes: uint32 pixels (exact: dimensions are capped at 65536,
- *   so a line sum of uint16 voxels stays below 2^32).  Float32 volumes: two
- *   float32 planes per image, the running sum and its compensation (the
- *   pixel's value is hi + lo).
+ *   so a line sum of uint16 voxels stays below 2^32).  Float32 volumes:
+ *   IEEE double pixels holding the compensated float32 line sum (float-float
+ *   accuracy, about 2^-46 relative to the sum of |V| along the line).
  * 2-D moments: T_ab = sum I[s][f] (s-off_s)^a (f-off_f)^b for a+b <= K (signed
  *   coordinates, the origin shift of Sec. 5), ordered degree ascending then
  *   a descending; (K+1)(K+2)/2 values per image, int128 for integer volumes,

@@ -223,7 +223,7 @@ def project(volume, K: int, dtype: int | None = None, stream=None):
     """Step 1 alone: the projection images as a list of CPU numpy arrays.
 
     Integer volumes give uint64 arrays [S_k, F_k]; float volumes give float64
-    arrays holding hi + lo.
+    arrays (the library's float images are doubles).
     """
     import torch
     dt = dtype_code(volume) if dtype is None else dtype
@@ -238,11 +238,8 @@ def project(volume, K: int, dtype: int | None = None, stream=None):
     for k in range(num_images(K)):
         S, F, _, _ = image_geometry(k, L, M, N)
         if dt == F32:
-            f = host.view(np.float32)
-            hi = f[at:at + S * F].astype(np.float64)
-            lo = f[at + S * F:at + 2 * S * F].astype(np.float64)
-            imgs.append((hi + lo).reshape(S, F))
-            at += 2 * S * F
+            imgs.append(host.view(np.float64)[at:at + S * F].copy().reshape(S, F))
+            at += S * F
         else:
             imgs.append(host.view(np.uint32)[at:at + S * F].astype(np.uint64).reshape(S, F))
             at += S * F

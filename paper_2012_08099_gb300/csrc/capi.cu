@@ -72,7 +72,7 @@ Layout layout(int64_t L, int64_t M, int64_t N, dpma_dtype dtype, int K) {
   Layout w;
   const bool fl = is_float(dtype);
   w.set = make_image_set(L, M, N, K, fl);
-  w.img_bytes = (size_t)w.set.total_elems * 4;
+  w.img_bytes = (size_t)w.set.total_elems * (fl ? 8 : 4);
   w.part_bytes = moments2d_partials_bytes(w.set, K, fl);
   w.m2d_bytes = (size_t)w.set.P * num_2d(K) * (fl ? 8 : 16);
   w.off_img = 0;

@@ -16,14 +16,13 @@ struct ImageSet {
   int P;
   int64_t S[kMaxImages], F[kMaxImages];
   int64_t off_s[kMaxImages], off_f[kMaxImages];
-  // element offset of image k inside the image buffer (uint32 pixels for
-  // integer volumes; for float volumes the hi plane starts here and the lo
-  // plane follows it at + S*F)
+  // pixel offset of image k inside the image buffer (uint32 pixels for
+  // integer volumes, IEEE double pixels for float volumes)
   int64_t base[kMaxImages];
-  int64_t total_elems;  // uint32 elements (int) or float elements (both planes)
+  int64_t total_elems;  // pixels of all images
 };
 
-inline ImageSet make_image_set(int64_t L, int64_t M, int64_t N, int K, bool is_float) {
+inline ImageSet make_image_set(int64_t L, int64_t M, int64_t N, int K, bool /*is_float*/) {
   ImageSet s{};
   s.P = num_images(K);
   int64_t at = 0;
@@ -32,7 +31,7 @@ inline ImageSet make_image_set(int64_t L, int64_t M, int64_t N, int K, bool is_f
     image_geom(k, L, M, N, &g);
     s.S[k] = g.S; s.F[k] = g.F; s.off_s[k] = g.off_s; s.off_f[k] = g.off_f;
     s.base[k] = at;
-    at += g.S * g.F * (is_float ? 2 : 1);
+    at += g.S * g.F;
   }
   s.total_elems = at;
   return s;

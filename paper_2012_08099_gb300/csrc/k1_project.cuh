@@ -23,12 +23,13 @@
 // shared slots merged by owner threads, images 7/8 (x+-y) through per-step
 // shared buffers.
 //
-// Float volumes keep every sum compensated: register accumulators are
-// Kahan pairs (sum, compensation), merges use the error-free TwoSum, and
-// global merges read the old value back from the atomic add to recover its
-// rounding error, which goes into the image's second (lo) plane.  The old
-// value is consumed one step later so the atomic's latency overlaps the
-// next step's work.  Integer volumes use exact uint32 sums and red.add.
+// Float volumes keep every sum compensated: each accumulator is a pair
+// (hi, lo) updated with the error-free TwoSum, so a pixel carries float-float
+// accuracy whatever the order and signs of its terms.  Partial sums that
+// leave a CTA are turned, with integer operations only, into the double that
+// equals hi + lo exactly and merged with red.global.add.f64 by the L2 (the
+// SMs execute no FP64 instruction).  Integer volumes use exact uint32 sums
+// and red.global.add.u32.
 #pragma once
 #include <cstdint>
 #include <type_traits>
@@ -115,89 +116,70 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       "l"(src), "r"(bytes), "r"(mbar)
       : "memory");
 }
-__device__ __forceinline__ void atom_add_v4(float* p, const float v[4], float o[4]) {
-  asm volatile("atom.global.v4.f32.add {%0,%1,%2,%3}, [%4], {%5,%6,%7,%8};"
-               : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3])
-               : "l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3])
-               : "memory");
-}
-__device__ __forceinline__ void red_add_v4(float* p, const float v[4]) {
-  asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(v[0]), "f"(v[1]),
-               "f"(v[2]), "f"(v[3])
-               : "memory");
-}
-
 // ---------------------------------------------------------------- float helpers
 
-// Kahan update of the pair (s, c) whose value is s - c.
-__device__ __forceinline__ void kahan(float& s, float& c, float v) {
-  const float y = __fsub_rn(v, c);
-  const float t = __fadd_rn(s, y);
-  c = __fsub_rn(__fsub_rn(t, s), y);
-  s = t;
+// (hi, lo) += v with the error-free TwoSum: hi + lo stays exact up to the
+// rounding of lo (at most one float32 rounding of the accumulated errors).
+__device__ __forceinline__ void ts_acc(float& hi, float& lo, float v) {
+  const float t = __fadd_rn(hi, v);
+  const float bb = __fsub_rn(t, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(v, bb));
+  lo = __fadd_rn(lo, e);
+  hi = t;
 }
 
-// Compensated merge of the pair (vh, vl) into a global (hi, lo) pixel, now.
-__device__ __forceinline__ void ff_emit_now(float* hi, float* lo, float vh, float vl) {
-  if (vh == 0.f && vl == 0.f) return;
-  const float old = atomicAdd(hi, vh);
-  float s, e;
-  two_sum(old, vh, s, e);
-  const float r = __fadd_rn(e, vl);
-  if (r != 0.f) atomicAdd(lo, r);
+// The double equal to hi + lo (both float32), built with integer operations.
+// hi + lo needs at most 48 significant bits when |lo| <= ulp(hi), so the
+// result is exact then; a wider gap rounds lo at 2^-52 relative to hi.
+__device__ __forceinline__ double ff_to_f64(float hi, float lo) {
+  const uint32_t bh = __float_as_uint(hi), bl = __float_as_uint(lo);
+  const int eh = (int)((bh >> 23) & 0xff), el = (int)((bl >> 23) & 0xff);
+  // signed integer mantissas and exponents: value = m * 2^e
+  long long mh = (long long)((bh & 0x7fffffu) | (eh ? 0x800000u : 0u));
+  long long ml = (long long)((bl & 0x7fffffu) | (el ? 0x800000u : 0u));
+  if (bh >> 31) mh = -mh;
+  if (bl >> 31) ml = -ml;
+  const int xh = (eh ? eh : 1) - 150, xl = (el ? el : 1) - 150;
+  if (ml == 0 && mh == 0) return 0.0;
+  // align both on the smaller exponent, keeping at most 62 bits
+  long long S;
+  int E;
+  if (mh == 0) { S = ml; E = xl; }
+  else if (ml == 0) { S = mh; E = xh; }
+  else {
+    const int lo_e = xh < xl ? xh : xl, hi_e = xh < xl ? xl : xh;
+    const long long mbig = xh < xl ? ml : mh, msmall = xh < xl ? mh : ml;
+    int d = hi_e - lo_e;
+    if (d <= 37) { S = (mbig << d) + msmall; E = lo_e; }
+    else { S = (mbig << 37) + (msmall >> (d - 37)); E = hi_e - 37; }
+  }
+  if (S == 0) return 0.0;
+  const unsigned long long sign = S < 0 ? (1ull << 63) : 0ull;
+  unsigned long long U = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
+  const int lz = __clzll(U);
+  const int msb = 63 - lz;                 // value = U * 2^E, U in [2^msb, 2^(msb+1))
+  if (msb > 52) {                          // round to 53 bits, nearest-even
+    const int sh = msb - 52;
+    const unsigned long long rem = U & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    U >>= sh;
+    E += sh;
+    if (rem > half || (rem == half && (U & 1))) ++U;
+    if (U >> 53) { U >>= 1; ++E; }
+  } else {
+    U <<= (52 - msb);
+    E -= (52 - msb);
+  }
+  const long long bexp = (long long)E + 52 + 1023;  // U in [2^52, 2^53)
+  if (bexp <= 0) return 0.0;                         // below the double range
+  const unsigned long long bits = sign | ((unsigned long long)bexp << 52) | (U & ((1ull << 52) - 1));
+  return __longlong_as_double((long long)bits);
 }
 
-// A deferred compensated merge of up to 4 consecutive pixels: issue() does
-// the atomic adds on the hi plane, consume() (later) turns the returned old
-// values into the exact rounding errors and adds them, together with the
-// pairs' low parts, to the lo plane.
-struct Pending {
-  float* hi;
-  int64_t lo_off;  // lo plane = hi + lo_off
-  int n;           // 0 = nothing pending
-  float vh[4], vl[4], old[4];
-  __device__ __forceinline__ void clear() { n = 0; hi = nullptr; lo_off = 0; }
-  __device__ __forceinline__ void set(float* h, int64_t off, int count, const float* a,
-                                      const float* b) {
-    hi = h; lo_off = off; n = count;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      vh[k] = k < count ? a[k] : 0.f;
-      vl[k] = k < count ? b[k] : 0.f;
-    }
-  }
-  __device__ __forceinline__ bool vec_ok() const {
-    return n == 4 && ((reinterpret_cast<uintptr_t>(hi) & 15) == 0) &&
-           ((reinterpret_cast<uintptr_t>(hi + lo_off) & 15) == 0);
-  }
-  __device__ __forceinline__ void issue() {
-    if (n == 0) return;
-    if (vec_ok()) {
-      atom_add_v4(hi, vh, old);
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) old[k] = (k < n && vh[k] != 0.f) ? atomicAdd(hi + k, vh[k]) : 0.f;
-    }
-  }
-  __device__ __forceinline__ void consume() {
-    if (n == 0) return;
-    float r[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      float s, e;
-      two_sum(old[k], vh[k], s, e);
-      r[k] = __fadd_rn(e, vl[k]);
-    }
-    if (vec_ok()) {
-      red_add_v4(hi + lo_off, r);
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (k < n && r[k] != 0.f) atomicAdd(hi + lo_off + k, r[k]);
-    }
-    n = 0;
-  }
-};
+// Merge the pair (hi, lo) into a global float pixel (a double), fire and forget.
+__device__ __forceinline__ void red_ff(double* p, float hi, float lo) {
+  if (hi == 0.f && lo == 0.f) return;
+  atomicAdd(p, ff_to_f64(hi, lo));
+}
 
 // ---------------------------------------------------------------- loads
 
@@ -295,7 +277,8 @@ template <typename T, int P, bool TMA>
 __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Params p) {
   using C = TileCfg<T, P>;
   constexpr bool FL = C::FL;
-  using A = typename std::conditional<FL, float, uint32_t>::type;
+  using A = typename std::conditional<FL, float, uint32_t>::type;    // accumulators
+  using IT = typename std::conditional<FL, double, uint32_t>::type;  // image pixels
   constexpr int TX = C::TX, XT = C::XT, NT = C::NT, NW = C::NW;
   constexpr int BYT = C::BYT, TY = C::TY;
   constexpr bool H3 = P > 3, H4 = P > 4, H5 = P > 5, H6 = P > 6, H7 = P > 7, H8 = P > 8;
@@ -327,7 +310,7 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
   const T* __restrict__ vol = static_cast<const T*>(p.vol);
   const int64_t L = p.L, M = p.M, N = p.N;
   const ImageSet& set = p.set;
-  A* img = static_cast<A*>(p.images);
+  IT* img = static_cast<IT*>(p.images);
   const bool vec_global =
       (L % R) == 0 && ((reinterpret_cast<uintptr_t>(p.vol) % (R * sizeof(T))) == 0);
 
@@ -383,8 +366,6 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
       a0[r][c] = 0; w3[r][c] = 0; w4[r][c] = 0; w5[r][c] = 0; w6[r][c] = 0;
       a0c[r][c] = 0.f; w3c[r][c] = 0.f; w4c[r][c] = 0.f; w5c[r][c] = 0.f; w6c[r][c] = 0.f;
     }
-  Pending pend;
-  pend.clear();
 
   int64_t seg_x0 = -1, seg_y0 = -1;
   bool aborted = false;
@@ -401,8 +382,8 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
 #pragma unroll
       for (int c = 0; c < R; ++c) {
         if (xs + c >= L) continue;
-        A* dst = img + set.base[0] + y * set.F[0] + xs + c;
-        if constexpr (FL) ff_emit_now(dst, dst + set.S[0] * set.F[0], a0[r][c], -a0c[r][c]);
+        IT* dst = img + set.base[0] + y * set.F[0] + xs + c;
+        if constexpr (FL) red_ff(dst, a0[r][c], a0c[r][c]);
         else if (a0[r][c]) atomicAdd(dst, a0[r][c]);
       }
     }
@@ -416,8 +397,8 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
           const int k = (int)(((q - zn) % R + R) % R);
           const int64_t f = xs + k + zn;
           if (f >= set.F[3]) continue;
-          A* dst = img + set.base[3] + y * set.F[3] + f;
-          if constexpr (FL) ff_emit_now(dst, dst + set.S[3] * set.F[3], w3[r][q], -w3c[r][q]);
+          IT* dst = img + set.base[3] + y * set.F[3] + f;
+          if constexpr (FL) red_ff(dst, w3[r][q], w3c[r][q]);
           else if (w3[r][q]) atomicAdd(dst, w3[r][q]);
         }
       }
@@ -432,8 +413,8 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
           const int k = (int)(((q + zn) % R + R) % R);
           const int64_t f = xs + k - zn + (N - 1);
           if (f < 0 || f >= set.F[4]) continue;
-          A* dst = img + set.base[4] + y * set.F[4] + f;
-          if constexpr (FL) ff_emit_now(dst, dst + set.S[4] * set.F[4], w4[r][q], -w4c[r][q]);
+          IT* dst = img + set.base[4] + y * set.F[4] + f;
+          if constexpr (FL) red_ff(dst, w4[r][q], w4c[r][q]);
           else if (w4[r][q]) atomicAdd(dst, w4[r][q]);
         }
       }
@@ -447,8 +428,8 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
 #pragma unroll
         for (int c = 0; c < R; ++c) {
           if (xs + c >= L) continue;
-          A* dst = img + set.base[5] + srow * set.F[5] + xs + c;
-          if constexpr (FL) ff_emit_now(dst, dst + set.S[5] * set.F[5], w5[q][c], -w5c[q][c]);
+          IT* dst = img + set.base[5] + srow * set.F[5] + xs + c;
+          if constexpr (FL) red_ff(dst, w5[q][c], w5c[q][c]);
           else if (w5[q][c]) atomicAdd(dst, w5[q][c]);
         }
       }
@@ -462,8 +443,8 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
 #pragma unroll
         for (int c = 0; c < R; ++c) {
           if (xs + c >= L) continue;
-          A* dst = img + set.base[6] + srow * set.F[6] + xs + c;
-          if constexpr (FL) ff_emit_now(dst, dst + set.S[6] * set.F[6], w6[q][c], -w6c[q][c]);
+          IT* dst = img + set.base[6] + srow * set.F[6] + xs + c;
+          if constexpr (FL) red_ff(dst, w6[q][c], w6c[q][c]);
           else if (w6[q][c]) atomicAdd(dst, w6[q][c]);
         }
       }
@@ -495,8 +476,6 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
       // ---- 1. wait for the slice (bounded)
       bool ok = true;
       if constexpr (TMA) ok = mbar_wait_bounded(smem_u32(&mbar[st]), (uint32_t)par);
-      // ---- 2. issue the deferred global merge of the previous step
-      if constexpr (FL) pend.issue();
 
       // ---- 3. the micro-tile
       A v[BYT][R];
@@ -525,12 +504,12 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
 #pragma unroll
         for (int c = 0; c < R; ++c) {
           if constexpr (FL) {
-            kahan(a0[r][c], a0c[r][c], v[r][c]);
-            if constexpr (H3) kahan(w3[r][(c + j) % R], w3c[r][(c + j) % R], v[r][c]);
-            if constexpr (H4) kahan(w4[r][(c - j + R) % R], w4c[r][(c - j + R) % R], v[r][c]);
-            if constexpr (H5) kahan(w5[(r + j) % BYT][c], w5c[(r + j) % BYT][c], v[r][c]);
+            ts_acc(a0[r][c], a0c[r][c], v[r][c]);
+            if constexpr (H3) ts_acc(w3[r][(c + j) % R], w3c[r][(c + j) % R], v[r][c]);
+            if constexpr (H4) ts_acc(w4[r][(c - j + R) % R], w4c[r][(c - j + R) % R], v[r][c]);
+            if constexpr (H5) ts_acc(w5[(r + j) % BYT][c], w5c[(r + j) % BYT][c], v[r][c]);
             if constexpr (H6)
-              kahan(w6[(r - j + R) % BYT][c], w6c[(r - j + R) % BYT][c], v[r][c]);
+              ts_acc(w6[(r - j + R) % BYT][c], w6c[(r - j + R) % BYT][c], v[r][c]);
           } else {
             a0[r][c] += v[r][c];
             if constexpr (H3) w3[r][(c + j) % R] += v[r][c];
@@ -550,14 +529,14 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
           csc[c] = 0.f;
 #pragma unroll
           for (int r = 1; r < BYT; ++r) {
-            if constexpr (FL) kahan(cs[c], csc[c], v[r][c]);
+            if constexpr (FL) ts_acc(cs[c], csc[c], v[r][c]);
             else cs[c] += v[r][c];
           }
         }
         A* s2 = slot2 + ((size_t)(sb * TY + ty) * XT + xl) * PW;
         if constexpr (FL) {
-          *reinterpret_cast<float4*>(s2) = make_float4(cs[0], -csc[0], cs[1], -csc[1]);
-          *reinterpret_cast<float4*>(s2 + 4) = make_float4(cs[2], -csc[2], cs[3], -csc[3]);
+          *reinterpret_cast<float4*>(s2) = make_float4(cs[0], csc[0], cs[1], csc[1]);
+          *reinterpret_cast<float4*>(s2 + 4) = make_float4(cs[2], csc[2], cs[3], csc[3]);
         } else {
           *reinterpret_cast<uint4*>(s2) = make_uint4(cs[0], cs[1], cs[2], cs[3]);
         }
@@ -569,14 +548,14 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
           rsc[r] = 0.f;
 #pragma unroll
           for (int c = 1; c < R; ++c) {
-            if constexpr (FL) kahan(rs[r], rsc[r], v[r][c]);
+            if constexpr (FL) ts_acc(rs[r], rsc[r], v[r][c]);
             else rs[r] += v[r][c];
           }
         }
         if constexpr (FL) {
           float lo[BYT];
 #pragma unroll
-          for (int r = 0; r < BYT; ++r) lo[r] = -rsc[r];
+          for (int r = 0; r < BYT; ++r) lo[r] = rsc[r];
           float oh, ol;
           if constexpr (BYT == 4) ff_reduce4_scatter(rs, lo, lane, oh, ol);
           else ff_reduce2_scatter(rs, lo, lane, oh, ol);
@@ -613,7 +592,7 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
                 d = v[r][c];
                 first = false;
               } else if constexpr (FL) {
-                kahan(d, dc, v[r][c]);
+                ts_acc(d, dc, v[r][c]);
               } else {
                 d += v[r][c];
               }
@@ -626,7 +605,7 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
                 const float old = atomicAdd(cell, d);
                 float sum, e;
                 two_sum(old, d, sum, e);
-                atomicAdd(cell + 1, __fadd_rn(e, -dc));
+                atomicAdd(cell + 1, __fadd_rn(e, dc));
               }
             } else {
               if (d) atomicAdd(cell, d);
@@ -649,7 +628,7 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
             A* d = (wx == 0) ? ex34 + ((size_t)(sb * 2 + 0) * BY + yl + r) * PW
                              : mb3 + ((size_t)((sb * TY + ty) * NW + wx - 1) * BYT + r) * PW;
             d[0] = sv;
-            if constexpr (FL) d[1] = -sc;
+            if constexpr (FL) d[1] = sc;
           }
         }
       }
@@ -667,7 +646,7 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
             A* d = (wx == NW - 1) ? ex34 + ((size_t)(sb * 2 + 1) * BY + yl + r) * PW
                                   : mb4 + ((size_t)((sb * TY + ty) * NW + wx + 1) * BYT + r) * PW;
             d[0] = sv;
-            if constexpr (FL) d[1] = -sc;
+            if constexpr (FL) d[1] = sc;
           }
         }
       }
@@ -684,8 +663,8 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
         if (ty > 0) {
           A* d = mb5 + ((size_t)(sb * TY + ty - 1) * XT + xl) * PW;
           if constexpr (FL) {
-            *reinterpret_cast<float4*>(d) = make_float4(out5[0], -out5c[0], out5[1], -out5c[1]);
-            *reinterpret_cast<float4*>(d + 4) = make_float4(out5[2], -out5c[2], out5[3], -out5c[3]);
+            *reinterpret_cast<float4*>(d) = make_float4(out5[0], out5c[0], out5[1], out5c[1]);
+            *reinterpret_cast<float4*>(d + 4) = make_float4(out5[2], out5c[2], out5[3], out5c[3]);
           } else {
             *reinterpret_cast<uint4*>(d) = make_uint4(out5[0], out5[1], out5[2], out5[3]);
           }
@@ -701,16 +680,13 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
         if (ty < TY - 1) {
           A* d = mb6 + ((size_t)(sb * TY + ty + 1) * XT + xl) * PW;
           if constexpr (FL) {
-            *reinterpret_cast<float4*>(d) = make_float4(out6[0], -out6c[0], out6[1], -out6c[1]);
-            *reinterpret_cast<float4*>(d + 4) = make_float4(out6[2], -out6c[2], out6[3], -out6c[3]);
+            *reinterpret_cast<float4*>(d) = make_float4(out6[0], out6c[0], out6[1], out6c[1]);
+            *reinterpret_cast<float4*>(d + 4) = make_float4(out6[2], out6c[2], out6[3], out6c[3]);
           } else {
             *reinterpret_cast<uint4*>(d) = make_uint4(out6[0], out6[1], out6[2], out6[3]);
           }
         }
       }
-
-      // ---- 8. finish the deferred merge issued in phase 2
-      if constexpr (FL) pend.consume();
 
       // ---- 9. step barrier, also agreeing on an abort
       if (__syncthreads_or(!ok)) {
@@ -728,7 +704,7 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
           for (int r = 0; r < BYT; ++r) {
             const A* d = mb3 + ((size_t)((sb * TY + ty) * NW + wx) * BYT + r) * PW;
             w3[r][j] = d[0];
-            if constexpr (FL) w3c[r][j] = -d[1];
+            if constexpr (FL) w3c[r][j] = d[1];
           }
         }
       }
@@ -739,7 +715,7 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
           for (int r = 0; r < BYT; ++r) {
             const A* d = mb4 + ((size_t)((sb * TY + ty) * NW + wx) * BYT + r) * PW;
             w4[r][q] = d[0];
-            if constexpr (FL) w4c[r][q] = -d[1];
+            if constexpr (FL) w4c[r][q] = d[1];
           }
         }
       }
@@ -749,7 +725,7 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
 #pragma unroll
           for (int c = 0; c < R; ++c) {
             w5[j % BYT][c] = d[c * PW];
-            if constexpr (FL) w5c[j % BYT][c] = -d[c * PW + 1];
+            if constexpr (FL) w5c[j % BYT][c] = d[c * PW + 1];
           }
         }
       }
@@ -760,7 +736,7 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
 #pragma unroll
           for (int c = 0; c < R; ++c) {
             w6[q][c] = d[c * PW];
-            if constexpr (FL) w6c[q][c] = -d[c * PW + 1];
+            if constexpr (FL) w6c[q][c] = d[c * PW + 1];
           }
         }
       }
@@ -770,13 +746,10 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
         if (ty == C::G_I5) {
           const int64_t srow = y0 + z;
           if (srow < set.S[5] && xs < L) {
-            A* dst = img + set.base[5] + srow * set.F[5] + xs;
+            IT* dst = img + set.base[5] + srow * set.F[5] + xs;
             const int n = (int)((L - xs) < R ? (L - xs) : R);
             if constexpr (FL) {
-              float lo[R];
-#pragma unroll
-              for (int c = 0; c < R; ++c) lo[c] = -out5c[c];
-              pend.set(dst, set.S[5] * set.F[5], n, out5, lo);
+              for (int c = 0; c < n; ++c) red_ff(dst + c, out5[c], out5c[c]);
             } else {
               for (int c = 0; c < n; ++c)
                 if (out5[c]) atomicAdd(dst + c, out5[c]);
@@ -788,13 +761,10 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
         if (ty == C::G_I6) {
           const int64_t srow = y0 + BY - 1 - z + (N - 1);
           if (srow >= 0 && srow < set.S[6] && xs < L) {
-            A* dst = img + set.base[6] + srow * set.F[6] + xs;
+            IT* dst = img + set.base[6] + srow * set.F[6] + xs;
             const int n = (int)((L - xs) < R ? (L - xs) : R);
             if constexpr (FL) {
-              float lo[R];
-#pragma unroll
-              for (int c = 0; c < R; ++c) lo[c] = -out6c[c];
-              pend.set(dst, set.S[6] * set.F[6], n, out6, lo);
+              for (int c = 0; c < n; ++c) red_ff(dst + c, out6[c], out6c[c]);
             } else {
               for (int c = 0; c < n; ++c)
                 if (out6[c]) atomicAdd(dst + c, out6[c]);
@@ -804,7 +774,7 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
       }
       if (ty == C::G_I2 && xs < L) {  // image 2: merge the TY column partials
         const int n = (int)((L - xs) < R ? (L - xs) : R);
-        A* dst = img + set.base[2] + z * set.F[2] + xs;
+        IT* dst = img + set.base[2] + z * set.F[2] + xs;
         if constexpr (FL) {
           float h[R], l[R];
 #pragma unroll
@@ -817,7 +787,7 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
               ff_add(h[c], l[c], e[0], e[1]);
             }
           }
-          pend.set(dst, set.S[2] * set.F[2], n, h, l);
+          for (int c = 0; c < n; ++c) red_ff(dst + c, h[c], l[c]);
         } else {
 #pragma unroll
           for (int c = 0; c < R; ++c) {
@@ -833,7 +803,7 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
           const int row = tx;
           const int64_t y = y0 + row;
           if (y < M) {
-            A* dst = img + set.base[1] + z * set.F[1] + y;
+            IT* dst = img + set.base[1] + z * set.F[1] + y;
             const int g = row / BYT, r = row % BYT;
             if constexpr (FL) {
               float h = 0.f, l = 0.f;
@@ -842,12 +812,8 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
                 const float* e = slot1 + ((size_t)((sb * TY + g) * NW + w) * BYT + r) * PW;
                 ff_add(h, l, e[0], e[1]);
               }
-              if (p.nxt == 1) {  // the whole row lies in this tile: the pixel is complete
-                dst[0] = h;
-                dst[set.S[1] * set.F[1]] = l;
-              } else {
-                pend.set(dst, set.S[1] * set.F[1], 1, &h, &l);
-              }
+              if (p.nxt == 1) dst[0] = ff_to_f64(h, l);  // the row lies in this tile: complete
+              else red_ff(dst, h, l);
             } else {
               uint32_t t = 0;
 #pragma unroll
@@ -870,10 +836,9 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
             const int64_t f = im == 0 ? x0 + z : x0 + XT - 1 - z + (N - 1);
             const A* cell = ex34 + ((size_t)(sb * 2 + im) * BY + row) * PW;
             if (f >= 0 && f < set.F[k]) {
-              A* dst = img + set.base[k] + y * set.F[k] + f;
+              IT* dst = img + set.base[k] + y * set.F[k] + f;
               if constexpr (FL) {
-                const float h = cell[0], l = cell[1];
-                pend.set(dst, set.S[k] * set.F[k], 1, &h, &l);
+                red_ff(dst, cell[0], cell[1]);
               } else {
                 if (cell[0]) atomicAdd(dst, cell[0]);
               }
@@ -890,8 +855,8 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
             const int k = 7 + im;
             const int64_t f = im == 0 ? x0 + y0 + idx : x0 - y0 - (BY - 1) + idx + (M - 1);
             if (f >= 0 && f < set.F[k]) {
-              A* dst = img + set.base[k] + z * set.F[k] + f;
-              if constexpr (FL) ff_emit_now(dst, dst + set.S[k] * set.F[k], cell[0], cell[1]);
+              IT* dst = img + set.base[k] + z * set.F[k] + f;
+              if constexpr (FL) red_ff(dst, cell[0], cell[1]);
               else if (cell[0]) atomicAdd(dst, cell[0]);
             }
             cell[0] = (A)0;
@@ -910,10 +875,6 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
         seg_end = (nx0 != seg_x0) || (ny0 != seg_y0);
       }
       if (seg_end) {
-        if constexpr (FL) {
-          pend.issue();
-          pend.consume();
-        }
         drain(seg_x0, seg_y0, z);
       }
     }

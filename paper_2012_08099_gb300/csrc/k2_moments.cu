@@ -13,8 +13,9 @@
 // row totals, and lane t then adds (s - off_s)^a F_b for the (a, b) pairs
 // it owns.  A CTA covers kRowsPerBlock rows of one image and writes one
 // partial vector per image pair; the combine kernel sums the partials.
-// Integer images accumulate exactly in int128; float images accumulate in
-// float-float (pairs of float32), so no FP64 arithmetic happens here.
+// Integer images accumulate exactly in int128; float images (doubles) are
+// split into float32 pairs with integer operations and accumulate in
+// float-float, so no FP64 arithmetic happens here.
 #include <cstdint>
 
 #include "dpma_internal.cuh"
@@ -125,6 +126,34 @@ __global__ void __launch_bounds__(kThreads) k2_int_kernel(K2Params p) {
 
 // float-float helpers -------------------------------------------------------
 
+// Split a double pixel (raw bits) into float32 hi + lo with integer
+// operations: hi is the mantissa rounded to 24 bits, lo the signed remainder
+// (rounded to 24 bits, i.e. 2^-48 relative to hi).  Pixels outside the
+// float32 exponent range are not produced by the projection of a float32
+// volume whose values stay below 2^110.
+__device__ __forceinline__ void f64_to_ff(unsigned long long b, float& hi, float& lo) {
+  const unsigned int sign = (unsigned int)(b >> 63) << 31;
+  const int e = (int)((b >> 52) & 0x7ff);
+  hi = 0.f;
+  lo = 0.f;
+  if (e == 0) return;  // zero (or a double far below the float range)
+  const unsigned long long m = (b & ((1ull << 52) - 1)) | (1ull << 52);  // value = m * 2^(e-1075)
+  unsigned long long mh = m >> 29;
+  long long rem = (long long)(m & ((1ull << 29) - 1));
+  if (rem >= (1ll << 28)) { mh += 1; rem -= (1ll << 29); }
+  int eh = e - 1075 + 29;  // hi = mh * 2^eh
+  if (mh == (1ull << 24)) { mh >>= 1; eh += 1; }
+  const int bexp = eh + 23 + 127;
+  if (bexp <= 0 || bexp >= 255) return;
+  hi = __uint_as_float(sign | ((unsigned int)bexp << 23) | (unsigned int)(mh & 0x7fffffu));
+  if (rem != 0) {
+    const float r = __int2float_rn((int)rem);          // |rem| < 2^29
+    const unsigned int rb = __float_as_uint(r);
+    const int re = (int)((rb >> 23) & 0xff) + (e - 1075);  // scale by 2^(e-1075)
+    if (re > 0 && re < 255) lo = __uint_as_float((rb & 0x807fffffu) ^ sign | ((unsigned int)re << 23));
+  }
+}
+
 // (hi, lo) * c for a float c whose products stay finite.
 __device__ __forceinline__ void ff_mul_f(float hi, float lo, float c, float& rh, float& rl) {
   float p, e;
@@ -141,8 +170,7 @@ __global__ void __launch_bounds__(kThreads) k2_f32_kernel(K2Params p) {
   const int64_t chunk = blk - p.blk_base[k];
   const int64_t S = p.set.S[k], F = p.set.F[k];
   const int64_t off_s = p.set.off_s[k], off_f = p.set.off_f[k];
-  const float* hi_plane = static_cast<const float*>(p.images) + p.set.base[k];
-  const float* lo_plane = hi_plane + S * F;
+  const unsigned long long* plane = static_cast<const unsigned long long*>(p.images) + p.set.base[k];
   const int K = p.K;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -165,10 +193,10 @@ __global__ void __launch_bounds__(kThreads) k2_f32_kernel(K2Params p) {
     float Fh[kMaxK + 1], Fl[kMaxK + 1];
 #pragma unroll
     for (int b = 0; b <= kMaxK; ++b) { Fh[b] = 0.f; Fl[b] = 0.f; }
-    const float* rh = hi_plane + s * F;
-    const float* rl = lo_plane + s * F;
+    const unsigned long long* row = plane + s * F;
     for (int64_t f = lane; f < F; f += 32) {
-      float th = rh[f], tl = rl[f];
+      float th, tl;
+      f64_to_ff(row[f], th, tl);
       if (th == 0.f && tl == 0.f) continue;
       const float c = (float)(f - off_f);
 #pragma unroll
