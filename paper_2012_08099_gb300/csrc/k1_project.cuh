@@ -334,11 +334,24 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
     x0 = (seg / p.nbands) * XT;
   };
 
-  // bulk-copy the slice of unit u into stage buffer st (one thread)
-  auto issue_unit = [&](int64_t u, int st) {
+  // Producer cursor (thread 0): the next unit to copy, advanced without
+  // divisions.  Units run z fastest, then band, then tile.
+  int64_t pc_x0 = 0, pc_y0 = 0, pc_z = 0;
+  if constexpr (TMA) {
+    if (tid == 0) decode(ub, pc_x0, pc_y0, pc_z);
+  }
+  auto advance = [&](int64_t& x0, int64_t& y0, int64_t& z) {
+    if (++z == N) {
+      z = 0;
+      y0 += BY;
+      if (y0 >= M) { y0 = 0; x0 += XT; }
+    }
+  };
+  // bulk-copy the slice at the producer cursor into stage buffer st
+  auto issue_next = [&](int st) {
     if constexpr (TMA) {
-      int64_t x0, y0, z;
-      decode(u, x0, y0, z);
+      const int64_t x0 = pc_x0, y0 = pc_y0, z = pc_z;
+      advance(pc_x0, pc_y0, pc_z);
       const int64_t rows = (M - y0) < BY ? (M - y0) : BY;
       const int64_t w = (L - x0) < XT ? (L - x0) : XT;
       const uint32_t row_bytes = (uint32_t)(w * sizeof(T));
@@ -353,7 +366,7 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
 
   if constexpr (TMA) {
     if (tid == 0)
-      for (int i = 0; i < STAGES && ub + i < ue; ++i) issue_unit(ub + i, i);
+      for (int i = 0; i < STAGES && ub + i < ue; ++i) issue_next(i);
   }
 
   // register state
@@ -367,7 +380,6 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
       a0c[r][c] = 0.f; w3c[r][c] = 0.f; w4c[r][c] = 0.f; w5c[r][c] = 0.f; w6c[r][c] = 0.f;
     }
 
-  int64_t seg_x0 = -1, seg_y0 = -1;
   bool aborted = false;
 
   // Emit what the registers hold for the current segment (its last step was
@@ -459,15 +471,18 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
   };
 
   int64_t s = 0;  // CTA step counter
-  int64_t u = ub;
+  int64_t u = ub;  // first unit of the current segment
   while (u < ue && !aborted) {
+    // one segment: a (tile, band) streamed over z in [za, zb)
+    int64_t x0, y0, za;
+    decode(u, x0, y0, za);
+    const int64_t zb = (N - za) < (ue - u) ? N : za + (ue - u);
+    int64_t z = za;
+    while (z < zb && !aborted) {
 #pragma unroll
     for (int j = 0; j < R; ++j) {  // unrolled so window slots are static: j == z % R
-      if (u >= ue || aborted) break;
-      int64_t x0, y0, z;
-      decode(u, x0, y0, z);
-      if ((int)(z % R) != j) continue;  // align the unroll phase with z
-      if (x0 != seg_x0 || y0 != seg_y0) { seg_x0 = x0; seg_y0 = y0; }
+      if (z >= zb || aborted) break;
+      if ((int)(z & (R - 1)) != j) continue;  // align the unroll phase with z
       const int st = (int)(s % STAGES);
       const int par = (int)((s / STAGES) & 1);
       const int sb = (int)(s & 1);  // shared double-buffer index
@@ -694,7 +709,7 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
         break;
       }
       if constexpr (TMA) {  // the slice is consumed: refill its stage
-        if (tid == 0 && u + STAGES < ue) issue_unit(u + STAGES, st);
+        if (tid == 0 && u + STAGES < ue) issue_next(st);
       }
 
       // ---- 10. receive the handed-over window pixels
@@ -867,17 +882,10 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
 
       ++s;
       ++u;
-      // segment end: the next unit starts another tile or band, or none is left
-      bool seg_end = (u >= ue);
-      if (!seg_end) {
-        int64_t nx0, ny0, nz;
-        decode(u, nx0, ny0, nz);
-        seg_end = (nx0 != seg_x0) || (ny0 != seg_y0);
-      }
-      if (seg_end) {
-        drain(seg_x0, seg_y0, z);
-      }
+      ++z;
     }
+    }
+    if (!aborted) drain(x0, y0, zb - 1);
   }
 
   if (aborted) {
