@@ -179,6 +179,32 @@ dpma_status dpma_image_moments(const void* images, int64_t L, int64_t M, int64_t
 dpma_status dpma_combine(const void* moments2d, dpma_dtype dtype, int K, void* out, void* stream,
                          int* status);
 
+/* ---------------- no device allocation ---------------- */
+
+/*
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot call cudaMalloc -- for example an application whose own memory
+ * pool already holds the device memory it may use, or a latency-critical
+ * loop that cannot accept cudaMalloc's device-wide synchronisation or its
+ * possible failure.
+ *
+ * Same result as dpma_moments_async (device `volume` and `out`, enqueued on
+ * `stream`, returns once enqueued), but the workspace -- projection images,
+ * partial sums, combine tables, status word -- lives in one static device
+ * array of 32 MiB (32 MiB - 64 KiB for the workspace) that every GPU which
+ * loads the library holds until the process exits; the call allocates no
+ * device memory.  Volumes needing more workspace than that (dpma_workspace_size)
+ * are refused with DPMA_ERR_REJECTED; 512^3 float32 at K = 6 fits.
+ *
+ * The first call on a device (with that device current) looks up the array's
+ * device address; make that first call before any stream capture.  Every
+ * call reuses the same array and clears what must start at zero; calls whose
+ * work overlaps on the GPU race on it and must be serialised by the caller.
+ * A combine self-check failure is not reported by this entry point.
+ */
+dpma_status dpma_moments_noalloc(const void* volume, int64_t L, int64_t M, int64_t N,
+                                 dpma_dtype dtype, int K, void* out, void* stream);
+
 /* ---------------- profiling aid ---------------- */
 
 /*

@@ -69,6 +69,7 @@ def lib():
                 "dpma_project": (ip, [vp, i64, i64, i64, ip, ip, vp, vp]),
                 "dpma_image_moments": (ip, [vp, i64, i64, i64, ip, ip, vp, vp, vp, sz]),
                 "dpma_combine": (ip, [vp, ip, ip, vp, vp, vp]),
+                "dpma_moments_noalloc": (ip, [vp, i64, i64, i64, ip, ip, vp, vp]),
                 "dpma_stage_timing": (ip, [ip]),
                 "dpma_stage_times": (ip, [ctypes.POINTER(ctypes.c_double), P64, ip]),
             }
@@ -268,6 +269,20 @@ def image_moments_of(volume, K: int, dtype: int | None = None):
         return f[:, :, 0] + f[:, :, 1]
     vals = int128_to_ints(h.view(np.int64))
     return [vals[k * npairs:(k + 1) * npairs] for k in range(P)]
+
+
+def moments_noalloc(volume, K: int, out, dtype: int | None = None, stream=None):
+    """All moments through the entry point that allocates no device memory.
+
+    For callers that cannot call cudaMalloc; the library's workspace is a
+    static 32 MiB device array shared by every call (see include/dpma.h).
+    Enqueued on ``stream`` (default: torch's current stream).
+    """
+    dt = dtype_code(volume) if dtype is None else dtype
+    L, M, N = _shape(volume)
+    _check(lib().dpma_moments_noalloc(ctypes.c_void_p(volume.data_ptr()), L, M, N, dt, K,
+                                      ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
 
 
 # ------------------------------------------------------------ profiling

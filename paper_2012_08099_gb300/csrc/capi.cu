@@ -212,6 +212,12 @@ size_t elem_size(dpma_dtype d) { return d == DPMA_U8 ? 1 : (d == DPMA_U16 ? 2 : 
 
 }  // namespace
 
+namespace dpma {
+// Records `msg` as the calling thread's last error (used by entry points
+// defined in other translation units).
+void set_last_error(const char* msg) { t_last_error = msg; }
+}  // namespace dpma
+
 extern "C" {
 
 int dpma_num_moments(int K) { return (K < 0 || K > DPMA_MAX_K) ? 0 : num_moments(K); }

@@ -261,4 +261,46 @@ cudaError_t launch_combine(const void* m2d, int K, bool is_float, void* out, int
   return cudaGetLastError();
 }
 
+// Packs the combine plan of order K into `words` (capacity in int64 words)
+// with the layout the combine kernels read; returns the word count, 0 if the
+// plan is unavailable or does not fit.  Host only, allocates no device memory.
+size_t pack_combine_plan(int K, int64_t* words, size_t capacity, int off[kMaxK + 1]) {
+  const CombinePlan* cp = combine_plan(K);
+  if (!cp) return 0;
+  size_t n = 0;
+  for (int k = 0; k <= kMaxK; ++k) off[k] = 0;
+  for (int d = 0; d <= K; ++d) {
+    const DegreePlan& g = cp->deg[d];
+    const size_t need = 2 + 2 * (size_t)g.nmono + (size_t)g.nmono * g.nmono;
+    if (n + need > capacity) return 0;
+    off[d] = (int)n;
+    words[n++] = g.D;
+    words[n++] = g.nmono;
+    for (int j = 0; j < g.nmono; ++j) words[n++] = g.img[j];
+    for (int j = 0; j < g.nmono; ++j) words[n++] = g.a[j];
+    for (int j = 0; j < g.nmono * g.nmono; ++j) words[n++] = g.C[j];
+  }
+  return n;
+}
+
+// Combine with a packed plan already resident at `dev_words` (device memory).
+cudaError_t launch_combine_packed(const int64_t* dev_words, const int off[kMaxK + 1],
+                                  const void* m2d, int K, bool is_float, void* out, int* status,
+                                  cudaStream_t st) {
+  CombParams p{};
+  p.plan = dev_words;
+  for (int n = 0; n <= kMaxK; ++n) p.off[n] = off[n];
+  p.K = K;
+  p.npairs = num_2d(K);
+  p.m2d = m2d;
+  p.out = out;
+  p.status = status;
+  const int nmom = num_moments(K);
+  const int threads = 64;
+  const int blocks = (nmom + threads - 1) / threads;
+  if (is_float) combine_f32_kernel<<<blocks, threads, 0, st>>>(p);
+  else combine_int_kernel<<<blocks, threads, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
 }  // namespace dpma
