@@ -52,10 +52,10 @@ constexpr int kStatusTimeout = 5;
 // floats) the register state needs a 4 x 2 micro-tile.
 template <typename T, int P> struct TileCfg {
   static constexpr bool FL = std::is_same<T, float>::value;
-  static constexpr bool SMALL = FL ? P >= 6 : P >= 5;    // 4 x 2 micro-tile
+  static constexpr bool SMALL = FL && P >= 6;            // 4 x 2 micro-tile
   static constexpr int BYT = SMALL ? 2 : 4;              // rows per thread
   static constexpr int TY = BY / BYT;                    // row groups
-  static constexpr int TX = FL ? (SMALL ? 32 : 64) : (SMALL ? 64 : 128);
+  static constexpr int TX = FL ? (SMALL ? 32 : 64) : 64;
   static constexpr int XT = R * TX;
   static constexpr int NT = TX * TY;
   static constexpr int NW = TX / 32;  // warps per row group
@@ -126,6 +126,25 @@ __device__ __forceinline__ void ts_acc(float& hi, float& lo, float v) {
   const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(v, bb));
   lo = __fadd_rn(lo, e);
   hi = t;
+}
+
+// Two independent TwoSum accumulations in one set of packed f32x2
+// instructions (sm_100 and later): (h0, l0) += v0 and (h1, l1) += v1.
+__device__ __forceinline__ void ts_acc2(float& h0, float& l0, float v0, float& h1, float& l1,
+                                        float v1) {
+  unsigned long long H, Lo, V, t, bb, x, y, e;
+  asm("mov.b64 %0, {%1,%2};" : "=l"(H) : "f"(h0), "f"(h1));
+  asm("mov.b64 %0, {%1,%2};" : "=l"(Lo) : "f"(l0), "f"(l1));
+  asm("mov.b64 %0, {%1,%2};" : "=l"(V) : "f"(v0), "f"(v1));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(H), "l"(V));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(bb) : "l"(t), "l"(H));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(x) : "l"(t), "l"(bb));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(x) : "l"(H), "l"(x));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(y) : "l"(V), "l"(bb));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(e) : "l"(x), "l"(y));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(Lo) : "l"(Lo), "l"(e));
+  asm("mov.b64 {%0,%1}, %2;" : "=f"(h0), "=f"(h1) : "l"(t));
+  asm("mov.b64 {%0,%1}, %2;" : "=f"(l0), "=f"(l1) : "l"(Lo));
 }
 
 // The double equal to hi + lo (both float32), built with integer operations.
@@ -514,17 +533,42 @@ __global__ void __launch_bounds__(TileCfg<T, P>::NT, 1) k1_project_kernel(K1Para
       }
 
       // ---- 4. images crossing the slice
+      if constexpr (FL) {
+        // packed pairs: adjacent columns for images 0, 5, 6; adjacent rows for
+        // the x-rotating windows of images 3, 4 (pairs stay fixed across j)
+#pragma unroll
+        for (int r = 0; r < BYT; ++r)
+#pragma unroll
+          for (int c = 0; c < R; c += 2) {
+            ts_acc2(a0[r][c], a0c[r][c], v[r][c], a0[r][c + 1], a0c[r][c + 1], v[r][c + 1]);
+            if constexpr (H5) {
+              const int q = (r + j) % BYT;
+              ts_acc2(w5[q][c], w5c[q][c], v[r][c], w5[q][c + 1], w5c[q][c + 1], v[r][c + 1]);
+            }
+            if constexpr (H6) {
+              const int q = (r - j + R) % BYT;
+              ts_acc2(w6[q][c], w6c[q][c], v[r][c], w6[q][c + 1], w6c[q][c + 1], v[r][c + 1]);
+            }
+          }
+#pragma unroll
+        for (int r = 0; r < BYT; r += 2)
+#pragma unroll
+          for (int c = 0; c < R; ++c) {
+            if constexpr (H3) {
+              const int q = (c + j) % R;
+              ts_acc2(w3[r][q], w3c[r][q], v[r][c], w3[r + 1][q], w3c[r + 1][q], v[r + 1][c]);
+            }
+            if constexpr (H4) {
+              const int q = (c - j + R) % R;
+              ts_acc2(w4[r][q], w4c[r][q], v[r][c], w4[r + 1][q], w4c[r + 1][q], v[r + 1][c]);
+            }
+          }
+      }
 #pragma unroll
       for (int r = 0; r < BYT; ++r)
 #pragma unroll
         for (int c = 0; c < R; ++c) {
           if constexpr (FL) {
-            ts_acc(a0[r][c], a0c[r][c], v[r][c]);
-            if constexpr (H3) ts_acc(w3[r][(c + j) % R], w3c[r][(c + j) % R], v[r][c]);
-            if constexpr (H4) ts_acc(w4[r][(c - j + R) % R], w4c[r][(c - j + R) % R], v[r][c]);
-            if constexpr (H5) ts_acc(w5[(r + j) % BYT][c], w5c[(r + j) % BYT][c], v[r][c]);
-            if constexpr (H6)
-              ts_acc(w6[(r - j + R) % BYT][c], w6c[(r - j + R) % BYT][c], v[r][c]);
           } else {
             a0[r][c] += v[r][c];
             if constexpr (H3) w3[r][(c + j) % R] += v[r][c];

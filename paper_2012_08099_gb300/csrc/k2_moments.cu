@@ -8,11 +8,12 @@
 // each image (its DRT listing); on a GPU the separable power sums above are
 // cheaper and exact, and they give identical results.
 //
-// One warp handles one image row at a time: lanes stride over the row and
-// accumulate F_b for b = 0..K, a butterfly reduction gives every lane the
-// row totals, and lane t then adds (s - off_s)^a F_b for the (a, b) pairs
-// it owns.  A CTA covers kRowsPerBlock rows of one image and writes one
-// partial vector per image pair; the combine kernel sums the partials.
+// One warp handles one image row: lanes stride over the row (four loads in
+// flight per lane) and accumulate F_b for b = 0..K, a butterfly reduction
+// gives every lane the row totals, and lane t then adds (s - off_s)^a F_b
+// for the (a, b) pairs it owns.  A CTA covers kRowsPerBlock = 8 rows of one
+// image, so a 512^3 volume's seven images give ~450 CTAs; each CTA writes
+// one partial vector and a small kernel sums the partials per image.
 // Integer images accumulate exactly in int128; float images (doubles) are
 // split into float32 pairs with integer operations and accumulate in
 // float-float, so no FP64 arithmetic happens here.
@@ -25,7 +26,7 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
-constexpr int kRowsPerBlock = 64;
+constexpr int kRowsPerBlock = kWarps;  // one image row per warp
 
 struct K2Params {
   const void* images;
@@ -76,16 +77,24 @@ __global__ void __launch_bounds__(kThreads) k2_int_kernel(K2Params p) {
 #pragma unroll
     for (int b = 0; b <= kMaxK; ++b) Fb[b] = 0;
     const uint32_t* row = img + s * F;
-    for (int64_t f = lane; f < F; f += 32) {
-      const uint32_t v = row[f];
-      if (!v) continue;
-      const int64_t c = f - off_f;
-      i128 t = (i128)v;
+    for (int64_t f0 = lane; f0 < F; f0 += 4 * 32) {
+      uint32_t vv[4];
 #pragma unroll
-      for (int b = 0; b <= kMaxK; ++b) {
-        if (b > K) break;
-        Fb[b] += t;
-        t *= (i128)c;
+      for (int q = 0; q < 4; ++q) {
+        const int64_t f = f0 + q * 32;
+        vv[q] = f < F ? __ldg(row + f) : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (!vv[q]) continue;
+        const int64_t c = f0 + q * 32 - off_f;
+        i128 t = (i128)vv[q];
+#pragma unroll
+        for (int b = 0; b <= kMaxK; ++b) {
+          if (b > K) break;
+          Fb[b] += t;
+          t *= (i128)c;
+        }
       }
     }
 #pragma unroll
@@ -194,16 +203,25 @@ __global__ void __launch_bounds__(kThreads) k2_f32_kernel(K2Params p) {
 #pragma unroll
     for (int b = 0; b <= kMaxK; ++b) { Fh[b] = 0.f; Fl[b] = 0.f; }
     const unsigned long long* row = plane + s * F;
-    for (int64_t f = lane; f < F; f += 32) {
-      float th, tl;
-      f64_to_ff(row[f], th, tl);
-      if (th == 0.f && tl == 0.f) continue;
-      const float c = (float)(f - off_f);
+    for (int64_t f0 = lane; f0 < F; f0 += 4 * 32) {
+      unsigned long long raw[4];
 #pragma unroll
-      for (int b = 0; b <= kMaxK; ++b) {
-        if (b > K) break;
-        ff_add(Fh[b], Fl[b], th, tl);
-        ff_mul_f(th, tl, c, th, tl);
+      for (int q = 0; q < 4; ++q) {
+        const int64_t f = f0 + q * 32;
+        raw[q] = f < F ? __ldg(row + f) : 0ull;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float th, tl;
+        f64_to_ff(raw[q], th, tl);
+        if (th == 0.f && tl == 0.f) continue;
+        const float c = (float)(f0 + q * 32 - off_f);
+#pragma unroll
+        for (int b = 0; b <= kMaxK; ++b) {
+          if (b > K) break;
+          ff_add(Fh[b], Fl[b], th, tl);
+          ff_mul_f(th, tl, c, th, tl);
+        }
       }
     }
 #pragma unroll
