@@ -1,9 +1,26 @@
 // Step 1 dispatch: element type and image count -> kernel instantiation.
 // The instantiations live in k1_inst_*.cu so they compile in parallel.
-#include "dpma_internal.cuh"
+#include <mutex>
+
+#include "k1_project.cuh"
 
 namespace dpma {
 namespace k1 {
+
+EncodeTiledFn encode_tiled_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
 cudaError_t launch_u8_lo(int P, const ProjectArgs& a, cudaStream_t st);
 cudaError_t launch_u8_hi(int P, const ProjectArgs& a, cudaStream_t st);
 cudaError_t launch_u16_lo(int P, const ProjectArgs& a, cudaStream_t st);
