@@ -133,6 +133,24 @@ __device__ __forceinline__ void ts_acc(float& hi, float& lo, float v) {
   hi = t;
 }
 
+// Two independent (hi, lo) += v updates as packed f32x2 operations.
+__device__ __forceinline__ void ts_acc2(float& h0, float& l0, float v0, float& h1, float& l1,
+                                        float v1) {
+  unsigned long long H, Lo, V, t, bb, x, y, e;
+  asm("mov.b64 %0, {%1,%2};" : "=l"(H) : "f"(h0), "f"(h1));
+  asm("mov.b64 %0, {%1,%2};" : "=l"(Lo) : "f"(l0), "f"(l1));
+  asm("mov.b64 %0, {%1,%2};" : "=l"(V) : "f"(v0), "f"(v1));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(H), "l"(V));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(bb) : "l"(t), "l"(H));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(x) : "l"(t), "l"(bb));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(x) : "l"(H), "l"(x));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(y) : "l"(V), "l"(bb));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(e) : "l"(x), "l"(y));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(Lo) : "l"(Lo), "l"(e));
+  asm("mov.b64 {%0,%1}, %2;" : "=f"(h0), "=f"(h1) : "l"(t));
+  asm("mov.b64 {%0,%1}, %2;" : "=f"(l0), "=f"(l1) : "l"(Lo));
+}
+
 // The double equal to a float32, from its bits (zero for subnormals, whose
 // magnitude is below 2^-126).
 __device__ __forceinline__ double f32_to_f64_bits(float f) {
@@ -273,16 +291,33 @@ __device__ __forceinline__ uint32_t u_rows_half(const uint32_t h[BYT], int tx) {
 
 // ---------------------------------------------------------------- kernel
 
+// Per-step exit buffer: one slot per merge task, in this order (slot counts
+// for a BY x XT tile): image 1 rows (BY), image 3 and image 4 edge pixels
+// (BY each), image 5 and image 6 exit rows (XT each), image 7 and image 8
+// diagonals (XT + BY - 1 each).  The images present for P images are a
+// prefix of this list, so P fixes the task count.
+template <int BY> struct ExitLayout {
+  static constexpr int kDiag = XT + BY - 1;
+  static constexpr int E1 = 0, E3 = BY, E4 = 2 * BY, E5 = 3 * BY, E6 = 3 * BY + XT;
+  static constexpr int E7 = 3 * BY + 2 * XT, E8 = E7 + kDiag, ET = E8 + kDiag;
+  static constexpr int ES = (ET + 3) & ~3;  // buffer stride: keeps 16-byte vector stores aligned
+  __host__ __device__ static constexpr int tasks(int P) {
+    return P <= 3 ? E3 : P == 4 ? E4 : P == 5 ? E5 : P == 6 ? E6 : P == 7 ? E7 : P == 8 ? E8 : ET;
+  }
+};
+
 template <typename T, int P, bool TMA>
-__global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __grid_constant__ CUtensorMap vmap) {
+__global__ void __launch_bounds__(NT, 1)
+    k1_project_kernel(K1Params p, const __grid_constant__ CUtensorMap vmap) {
   using C = TileCfg<T, P>;
   constexpr bool FL = C::FL;
   using A = typename std::conditional<FL, float, uint32_t>::type;    // accumulators
   using IT = typename std::conditional<FL, double, uint32_t>::type;  // image pixels
   constexpr int BYT = C::BYT, BY = C::BY, STAGES = C::STAGES;
   constexpr bool H3 = P > 3, H4 = P > 4, H5 = P > 5, H6 = P > 6, H7 = P > 7, H8 = P > 8;
-  constexpr int PW = FL ? 2 : 1;  // words per pixel pair in shared buffers
-  constexpr int kDiag = XT + BY - 1;
+  constexpr int PW = FL ? 2 : 1;  // words per slot (float slots hold hi, lo)
+  using X = ExitLayout<BY>;
+  constexpr int NTASK = X::tasks(P);
 
   // ---- shared memory (every section 128-byte aligned)
   extern __shared__ __align__(128) unsigned char smem[];
@@ -294,15 +329,11 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
   };
   uint64_t* mbar = reinterpret_cast<uint64_t*>(take(sizeof(uint64_t) * STAGES));
   T* stage = TMA ? reinterpret_cast<T*>(take(sizeof(T) * STAGES * BY * XT)) : nullptr;
-  A* slot2 = reinterpret_cast<A*>(take(sizeof(A) * PW * 2 * TY * XT));   // [2][TY][XT]
-  A* slot1 = reinterpret_cast<A*>(take(sizeof(A) * PW * 2 * BY));        // [2][BY]
-  A* ex3 = reinterpret_cast<A*>(take(sizeof(A) * PW * 2 * BY));          // [2][BY]
-  A* ex4 = reinterpret_cast<A*>(take(sizeof(A) * PW * 2 * BY));
-  A* mb5 = reinterpret_cast<A*>(take(sizeof(A) * PW * 2 * TY * XT));     // [2][TY][XT]
+  A* slot2 = reinterpret_cast<A*>(take(sizeof(A) * PW * 2 * TY * XT));  // [2][TY][XT]
+  A* mb5 = reinterpret_cast<A*>(take(sizeof(A) * PW * 2 * TY * XT));    // [2][TY][XT]
   A* mb6 = reinterpret_cast<A*>(take(sizeof(A) * PW * 2 * TY * XT));
-  A* er5 = reinterpret_cast<A*>(take(sizeof(A) * PW * 2 * XT));          // [2][XT]
-  A* er6 = reinterpret_cast<A*>(take(sizeof(A) * PW * 2 * XT));
-  A* dg = reinterpret_cast<A*>(take(sizeof(A) * PW * 2 * 2 * kDiag));    // [2][2][kDiag]
+  A* xb = reinterpret_cast<A*>(take(sizeof(A) * PW * 2 * X::ES));       // [2][ES]
+  int4* roles = reinterpret_cast<int4*>(take(sizeof(int4) * NTASK));
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -318,7 +349,7 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
   const int64_t ub = p.units * (int64_t)blockIdx.x / gridDim.x;
   const int64_t ue = p.units * (int64_t)(blockIdx.x + 1) / gridDim.x;
 
-  for (int i = tid; i < 2 * 2 * kDiag * PW; i += NT) dg[i] = (A)0;
+  for (int i = tid; i < 2 * X::ES * PW; i += NT) xb[i] = (A)0;
   if constexpr (TMA) {
     if (tid == 0) {
       for (int i = 0; i < STAGES; ++i) mbar_init(smem_u32(&mbar[i]), 1);
@@ -363,17 +394,26 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
   // register state
   A a0[BYT][R], w3[BYT][R], w4[BYT][R], w5[BYT][R], w6[BYT][R];
   float a0c[BYT][R], w3c[BYT][R], w4c[BYT][R], w5c[BYT][R], w6c[BYT][R];
+  auto clear_state = [&]() {
 #pragma unroll
-  for (int r = 0; r < BYT; ++r)
+    for (int r = 0; r < BYT; ++r)
 #pragma unroll
-    for (int c = 0; c < R; ++c) {
-      a0[r][c] = 0; w3[r][c] = 0; w4[r][c] = 0; w5[r][c] = 0; w6[r][c] = 0;
-      a0c[r][c] = 0.f; w3c[r][c] = 0.f; w4c[r][c] = 0.f; w5c[r][c] = 0.f; w6c[r][c] = 0.f;
-    }
+      for (int c = 0; c < R; ++c) {
+        a0[r][c] = 0; w3[r][c] = 0; w4[r][c] = 0; w5[r][c] = 0; w6[r][c] = 0;
+        if constexpr (FL) {
+          a0c[r][c] = 0.f; w3c[r][c] = 0.f; w4c[r][c] = 0.f; w5c[r][c] = 0.f; w6c[r][c] = 0.f;
+        }
+      }
+  };
+  clear_state();
 
   auto emit = [&](IT* dst, A hi, float lo) {
     if constexpr (FL) emit_ff(dst, hi, lo);
     else emit_u(dst, hi);
+  };
+  auto lo_of = [&](const float (&a)[BYT][R], int r, int c) -> float {
+    if constexpr (FL) return a[r][c];
+    else return 0.f;
   };
 
   // Emit what the registers hold for the current segment (its last step was
@@ -388,7 +428,7 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
 #pragma unroll
       for (int c = 0; c < R; ++c) {
         if (xs + c >= L) continue;
-        emit(img + set.base[0] + y * set.F[0] + xs + c, a0[r][c], a0c[r][c]);
+        emit(img + set.base[0] + y * set.F[0] + xs + c, a0[r][c], lo_of(a0c, r, c));
       }
     }
     if constexpr (H3) {  // logical k = (q - zn) mod R holds pixel x+z = xs + k + zn
@@ -400,7 +440,7 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
         for (int q = 0; q < R; ++q) {
           const int k = (int)(((q - zn) % R + R) % R);
           const int64_t f = xs + k + zn;
-          if (f < set.F[3]) emit(img + set.base[3] + y * set.F[3] + f, w3[r][q], w3c[r][q]);
+          if (f < set.F[3]) emit(img + set.base[3] + y * set.F[3] + f, w3[r][q], lo_of(w3c, r, q));
         }
       }
     }
@@ -413,7 +453,8 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
         for (int q = 0; q < R; ++q) {
           const int k = (int)(((q + zn) % R + R) % R);
           const int64_t f = xs + k - zn + (N - 1);
-          if (f >= 0 && f < set.F[4]) emit(img + set.base[4] + y * set.F[4] + f, w4[r][q], w4c[r][q]);
+          if (f >= 0 && f < set.F[4])
+            emit(img + set.base[4] + y * set.F[4] + f, w4[r][q], lo_of(w4c, r, q));
         }
       }
     }
@@ -425,7 +466,7 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
         if (srow >= set.S[5]) continue;
 #pragma unroll
         for (int c = 0; c < R; ++c)
-          if (xs + c < L) emit(img + set.base[5] + srow * set.F[5] + xs + c, w5[q][c], w5c[q][c]);
+          if (xs + c < L) emit(img + set.base[5] + srow * set.F[5] + xs + c, w5[q][c], lo_of(w5c, q, c));
       }
     }
     if constexpr (H6) {  // logical k = (q + zn) mod BYT holds row y-z+N-1 = yt + k - zn + N-1
@@ -436,16 +477,55 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
         if (srow < 0 || srow >= set.S[6]) continue;
 #pragma unroll
         for (int c = 0; c < R; ++c)
-          if (xs + c < L) emit(img + set.base[6] + srow * set.F[6] + xs + c, w6[q][c], w6c[q][c]);
+          if (xs + c < L) emit(img + set.base[6] + srow * set.F[6] + xs + c, w6[q][c], lo_of(w6c, q, c));
       }
     }
-#pragma unroll
-    for (int r = 0; r < BYT; ++r)
-#pragma unroll
-      for (int c = 0; c < R; ++c) {
-        a0[r][c] = 0; w3[r][c] = 0; w4[r][c] = 0; w5[r][c] = 0; w6[r][c] = 0;
-        a0c[r][c] = 0.f; w3c[r][c] = 0.f; w4c[r][c] = 0.f; w5c[r][c] = 0.f; w6c[r][c] = 0.f;
+    clear_state();
+  };
+
+  // Destination of every merge task for the segment at (x0, y0): pixel index
+  // base + z * zs, taken for z >= zmin (zmin = INT_MAX: no pixel).
+  auto set_roles = [&](int64_t x0, int64_t y0) {
+    constexpr int kNever = 0x7fffffff;
+    for (int t = tid; t < NTASK; t += NT) {
+      int64_t base = 0;
+      int64_t zs = 0;
+      int64_t zmin = kNever;
+      if (t < X::E3) {  // image 1: pixel (z, y)
+        const int64_t y = y0 + t;
+        if (y < M) { base = set.base[1] + y; zs = set.F[1]; zmin = 0; }
+      } else if (t < X::E5) {  // images 3/4: the pixel leaving the tile edge of row y
+        const bool i3 = t < X::E4;
+        const int64_t y = y0 + (i3 ? t - X::E3 : t - X::E4);
+        if (y < M) {
+          if (i3) {  // leaves at x = x0: f = x0 + z
+            base = set.base[3] + y * set.F[3] + x0; zs = 1; zmin = 0;
+          } else {  // leaves at x = x0 + XT - 1: f = x0 + XT - 1 - z + N - 1 < F4 iff z >= x0 + XT - L
+            base = set.base[4] + y * set.F[4] + x0 + XT + N - 2; zs = -1;
+            zmin = x0 + XT - L > 0 ? x0 + XT - L : 0;
+          }
+        }
+      } else if (t < X::E7) {  // images 5/6: the row leaving the band edge, column x
+        const bool i5 = t < X::E6;
+        const int64_t x = x0 + (i5 ? t - X::E5 : t - X::E6);
+        if (x < L) {
+          if (i5) {  // row y0 + z
+            base = set.base[5] + y0 * set.F[5] + x; zs = set.F[5]; zmin = 0;
+          } else {  // row y0 + BY - 1 - z + N - 1 < S6 iff z >= y0 + BY - M
+            base = set.base[6] + (y0 + BY + N - 2) * set.F[6] + x; zs = -set.F[6];
+            zmin = y0 + BY - M > 0 ? y0 + BY - M : 0;
+          }
+        }
+      } else {  // images 7/8: diagonal idx of the tile
+        const bool i7 = t < X::E8;
+        const int64_t idx = i7 ? t - X::E7 : t - X::E8;
+        const int k = i7 ? 7 : 8;
+        const int64_t f = i7 ? x0 + y0 + idx : x0 - y0 - (BY - 1) + idx + (M - 1);
+        if (f >= 0 && f < set.F[k]) { base = set.base[k] + f; zs = set.F[k]; zmin = 0; }
       }
+      roles[t] = make_int4((int)(uint32_t)(uint64_t)base, (int)((uint64_t)base >> 32), (int)zs,
+                           (int)zmin);
+    }
   };
 
   bool aborted = false;
@@ -461,6 +541,13 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
     const int ncol = (int)((L - xs) <= 0 ? 0 : ((L - xs) < R ? (L - xs) : R));
     const int nrow = (int)((M - yt) <= 0 ? 0 : ((M - yt) < BYT ? (M - yt) : BYT));
     const bool full = (ncol == R) && (nrow == BYT);
+    // image 2 merge: column col2 of the tile, quarter part2 of the row groups
+    const int col2 = tid >> 2, part2 = tid & 3;
+    const bool ok2 = part2 == 0 && x0 + col2 < L;
+    IT* const img2 = img + set.base[2] + x0 + col2;
+    const int64_t F2 = set.F[2];
+    set_roles(x0, y0);
+    __syncthreads();
     int64_t z = za;
     while (z < zb && !aborted) {
 #pragma unroll
@@ -470,6 +557,7 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
       const int st = (int)(s & (STAGES - 1));
       const int par = (int)((s / STAGES) & 1);
       const int sb = (int)(s & 1);  // shared double-buffer index
+      A* const xc = xb + (size_t)sb * X::ES * PW;
 
       // ---- 1. the micro-tile of slice z
       bool ok = true;
@@ -496,25 +584,37 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
       }
 
       // ---- 2. images crossing the slice
+      if constexpr (FL) {
 #pragma unroll
-      for (int r = 0; r < BYT; ++r)
+        for (int r = 0; r < BYT; ++r)
 #pragma unroll
-        for (int c = 0; c < R; ++c) {
-          if constexpr (FL) {
-            ts_acc(a0[r][c], a0c[r][c], v[r][c]);
-            if constexpr (H3) ts_acc(w3[r][(c + j) % R], w3c[r][(c + j) % R], v[r][c]);
-            if constexpr (H4) ts_acc(w4[r][(c - j + R) % R], w4c[r][(c - j + R) % R], v[r][c]);
-            if constexpr (H5) ts_acc(w5[(r + j) % BYT][c], w5c[(r + j) % BYT][c], v[r][c]);
+          for (int c = 0; c < R; c += 2) {
+            ts_acc2(a0[r][c], a0c[r][c], v[r][c], a0[r][c + 1], a0c[r][c + 1], v[r][c + 1]);
+            if constexpr (H3)
+              ts_acc2(w3[r][(c + j) % R], w3c[r][(c + j) % R], v[r][c], w3[r][(c + 1 + j) % R],
+                      w3c[r][(c + 1 + j) % R], v[r][c + 1]);
+            if constexpr (H4)
+              ts_acc2(w4[r][(c - j + R) % R], w4c[r][(c - j + R) % R], v[r][c],
+                      w4[r][(c + 1 - j + R) % R], w4c[r][(c + 1 - j + R) % R], v[r][c + 1]);
+            if constexpr (H5)
+              ts_acc2(w5[(r + j) % BYT][c], w5c[(r + j) % BYT][c], v[r][c], w5[(r + j) % BYT][c + 1],
+                      w5c[(r + j) % BYT][c + 1], v[r][c + 1]);
             if constexpr (H6)
-              ts_acc(w6[(r - j + R) % BYT][c], w6c[(r - j + R) % BYT][c], v[r][c]);
-          } else {
+              ts_acc2(w6[(r - j + R) % BYT][c], w6c[(r - j + R) % BYT][c], v[r][c],
+                      w6[(r - j + R) % BYT][c + 1], w6c[(r - j + R) % BYT][c + 1], v[r][c + 1]);
+          }
+      } else {
+#pragma unroll
+        for (int r = 0; r < BYT; ++r)
+#pragma unroll
+          for (int c = 0; c < R; ++c) {
             a0[r][c] += v[r][c];
             if constexpr (H3) w3[r][(c + j) % R] += v[r][c];
             if constexpr (H4) w4[r][(c - j + R) % R] += v[r][c];
             if constexpr (H5) w5[(r + j) % BYT][c] += v[r][c];
             if constexpr (H6) w6[(r - j + R) % BYT][c] += v[r][c];
           }
-        }
+      }
 
       // ---- 3. images in the slice: column sums (2), row sums (1), diagonals (7, 8)
       {
@@ -554,13 +654,13 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
           float oh, ol;
           ff_rows_half<BYT>(rs, rsc, tx, oh, ol);
           if ((tx & (per - 1)) == 0) {
-            A* d = slot1 + ((size_t)sb * BY + yl + tx / per) * PW;
+            A* d = xc + (size_t)(X::E1 + yl + tx / per) * PW;
             d[0] = oh;
             d[1] = ol;
           }
         } else {
           const uint32_t t = u_rows_half<BYT>(rs, tx);
-          if ((tx & (per - 1)) == 0) slot1[(size_t)sb * BY + yl + tx / per] = t;
+          if ((tx & (per - 1)) == 0) xc[X::E1 + yl + tx / per] = t;
         }
       }
       if constexpr (H7 || H8) {
@@ -587,7 +687,7 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
             }
             // local index x_l + y_l (image 7) or x_l - y_l + BY - 1 (image 8)
             const int idx = im == 0 ? xl + yl + k : xl - yl + (BY - BYT) + k;
-            A* cell = dg + ((size_t)(sb * 2 + im) * kDiag + idx) * PW;
+            A* cell = xc + (size_t)((im == 0 ? X::E7 : X::E8) + idx) * PW;
             if constexpr (FL) {
               if (d != 0.f || dc != 0.f) {
                 const float old = atomicAdd(cell, d);
@@ -607,13 +707,16 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
 #pragma unroll
         for (int r = 0; r < BYT; ++r) {
           const A sv = w3[r][j];
-          const float sc = w3c[r][j];
           const A rv = __shfl_down_sync(0xffffffffu, sv, 1, 16);
-          const float rc = __shfl_down_sync(0xffffffffu, sc, 1, 16);
           w3[r][j] = (tx == TX - 1) ? (A)0 : rv;
-          w3c[r][j] = (tx == TX - 1) ? 0.f : rc;
+          float sc = 0.f;
+          if constexpr (FL) {
+            sc = w3c[r][j];
+            const float rc = __shfl_down_sync(0xffffffffu, sc, 1, 16);
+            w3c[r][j] = (tx == TX - 1) ? 0.f : rc;
+          }
           if (tx == 0) {  // leaves the tile: complete for this CTA
-            A* d = ex3 + ((size_t)sb * BY + yl + r) * PW;
+            A* d = xc + (size_t)(X::E3 + yl + r) * PW;
             d[0] = sv;
             if constexpr (FL) d[1] = sc;
           }
@@ -624,24 +727,27 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
 #pragma unroll
         for (int r = 0; r < BYT; ++r) {
           const A sv = w4[r][q];
-          const float sc = w4c[r][q];
           const A rv = __shfl_up_sync(0xffffffffu, sv, 1, 16);
-          const float rc = __shfl_up_sync(0xffffffffu, sc, 1, 16);
           w4[r][q] = (tx == 0) ? (A)0 : rv;
-          w4c[r][q] = (tx == 0) ? 0.f : rc;
+          float sc = 0.f;
+          if constexpr (FL) {
+            sc = w4c[r][q];
+            const float rc = __shfl_up_sync(0xffffffffu, sc, 1, 16);
+            w4c[r][q] = (tx == 0) ? 0.f : rc;
+          }
           if (tx == TX - 1) {
-            A* d = ex4 + ((size_t)sb * BY + yl + r) * PW;
+            A* d = xc + (size_t)(X::E4 + yl + r) * PW;
             d[0] = sv;
             if constexpr (FL) d[1] = sc;
           }
         }
       }
       // images 5/6: the leaving window row goes to the group above (5) or
-      // below (6); the band's edge group puts it in the exit row
+      // below (6); the band's edge group puts it in the exit buffer
       if constexpr (H5) {
         const int q = j % BYT;
         A* d = ty > 0 ? mb5 + ((size_t)(sb * TY + ty - 1) * XT + xl) * PW
-                      : er5 + ((size_t)sb * XT + xl) * PW;
+                      : xc + (size_t)(X::E5 + xl) * PW;
         if constexpr (FL) {
           *reinterpret_cast<float4*>(d) = make_float4(w5[q][0], w5c[q][0], w5[q][1], w5c[q][1]);
           *reinterpret_cast<float4*>(d + 4) = make_float4(w5[q][2], w5c[q][2], w5[q][3], w5c[q][3]);
@@ -649,12 +755,15 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
           *reinterpret_cast<uint4*>(d) = make_uint4(w5[q][0], w5[q][1], w5[q][2], w5[q][3]);
         }
 #pragma unroll
-        for (int c = 0; c < R; ++c) { w5[q][c] = 0; w5c[q][c] = 0.f; }
+        for (int c = 0; c < R; ++c) {
+          w5[q][c] = 0;
+          if constexpr (FL) w5c[q][c] = 0.f;
+        }
       }
       if constexpr (H6) {
         const int q = (BYT - 1 - j + R) % BYT;
         A* d = ty < TY - 1 ? mb6 + ((size_t)(sb * TY + ty + 1) * XT + xl) * PW
-                           : er6 + ((size_t)sb * XT + xl) * PW;
+                           : xc + (size_t)(X::E6 + xl) * PW;
         if constexpr (FL) {
           *reinterpret_cast<float4*>(d) = make_float4(w6[q][0], w6c[q][0], w6[q][1], w6c[q][1]);
           *reinterpret_cast<float4*>(d + 4) = make_float4(w6[q][2], w6c[q][2], w6[q][3], w6c[q][3]);
@@ -662,7 +771,10 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
           *reinterpret_cast<uint4*>(d) = make_uint4(w6[q][0], w6[q][1], w6[q][2], w6[q][3]);
         }
 #pragma unroll
-        for (int c = 0; c < R; ++c) { w6[q][c] = 0; w6c[q][c] = 0.f; }
+        for (int c = 0; c < R; ++c) {
+          w6[q][c] = 0;
+          if constexpr (FL) w6c[q][c] = 0.f;
+        }
       }
 
       // ---- 5. step barrier, also agreeing on an abort
@@ -679,10 +791,14 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
         if (ty < TY - 1) {
           const int q = j % BYT;
           const A* d = mb5 + ((size_t)(sb * TY + ty) * XT + xl) * PW;
-#pragma unroll
-          for (int c = 0; c < R; ++c) {
-            w5[q][c] = d[c * PW];
-            if constexpr (FL) w5c[q][c] = d[c * PW + 1];
+          if constexpr (FL) {
+            const float4 e0 = *reinterpret_cast<const float4*>(d);
+            const float4 e1 = *reinterpret_cast<const float4*>(d + 4);
+            w5[q][0] = e0.x; w5c[q][0] = e0.y; w5[q][1] = e0.z; w5c[q][1] = e0.w;
+            w5[q][2] = e1.x; w5c[q][2] = e1.y; w5[q][3] = e1.z; w5c[q][3] = e1.w;
+          } else {
+            const uint4 e0 = *reinterpret_cast<const uint4*>(d);
+            w5[q][0] = e0.x; w5[q][1] = e0.y; w5[q][2] = e0.z; w5[q][3] = e0.w;
           }
         }
       }
@@ -690,10 +806,14 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
         if (ty > 0) {
           const int q = (BYT - 1 - j + R) % BYT;
           const A* d = mb6 + ((size_t)(sb * TY + ty) * XT + xl) * PW;
-#pragma unroll
-          for (int c = 0; c < R; ++c) {
-            w6[q][c] = d[c * PW];
-            if constexpr (FL) w6c[q][c] = d[c * PW + 1];
+          if constexpr (FL) {
+            const float4 e0 = *reinterpret_cast<const float4*>(d);
+            const float4 e1 = *reinterpret_cast<const float4*>(d + 4);
+            w6[q][0] = e0.x; w6c[q][0] = e0.y; w6[q][1] = e0.z; w6c[q][1] = e0.w;
+            w6[q][2] = e1.x; w6c[q][2] = e1.y; w6[q][3] = e1.z; w6c[q][3] = e1.w;
+          } else {
+            const uint4 e0 = *reinterpret_cast<const uint4*>(d);
+            w6[q][0] = e0.x; w6[q][1] = e0.y; w6[q][2] = e0.z; w6[q][3] = e0.w;
           }
         }
       }
@@ -701,12 +821,11 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
       // ---- 7. merge this step's complete results into the images
       // (a) image 2, one quarter of a column's TY partials per thread
       {
-        const int col = tid >> 2, part = tid & 3;
         A h = 0;
         float l = 0.f;
 #pragma unroll
-        for (int g = part * (TY / 4); g < (part + 1) * (TY / 4); ++g) {
-          const A* e = slot2 + ((size_t)(sb * TY + g) * XT + col) * PW;
+        for (int g = part2 * (TY / 4); g < (part2 + 1) * (TY / 4); ++g) {
+          const A* e = slot2 + ((size_t)(sb * TY + g) * XT + col2) * PW;
           if constexpr (FL) ff_add(h, l, e[0], e[1]);
           else h += e[0];
         }
@@ -719,55 +838,25 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
             h += __shfl_xor_sync(0xffffffffu, h, m);
           }
         }
-        if (part == 0 && x0 + col < L) emit(img + set.base[2] + z * set.F[2] + x0 + col, h, l);
+        if (ok2) emit(img2 + z * F2, h, l);
       }
-      // (b) the other per-step results: image 1 rows, image 3/4 edge pixels,
-      // image 5/6 exit rows, image 7/8 diagonals
-      {
-        constexpr int nB = 3 * BY + 2 * XT + (H7 ? kDiag : 0) + (H8 ? kDiag : 0);
-        for (int t = tid; t < nB; t += NT) {
-          int e = t;
-          if (e < BY) {  // image 1: (z, y0 + e)
-            const int64_t y = y0 + e;
-            const A* c = slot1 + ((size_t)sb * BY + e) * PW;
-            if (y < M) emit(img + set.base[1] + z * set.F[1] + y, c[0], FL ? c[PW - 1] : 0.f);
-            continue;
+      // (b) the exit buffer, one slot per task
+#pragma unroll
+      for (int i = 0; i < (NTASK + NT - 1) / NT; ++i) {
+        const int t = tid + i * NT;
+        if (t < NTASK) {
+          const int4 rd = roles[t];
+          A* c = xc + (size_t)t * PW;
+          const A hv = c[0];
+          float lv = 0.f;
+          if constexpr (FL) lv = c[1];
+          if (t >= X::E7) {  // diagonal cells accumulate: clear for the step after next
+            c[0] = (A)0;
+            if constexpr (FL) c[1] = 0.f;
           }
-          e -= BY;
-          if (e < 2 * BY) {  // images 3/4: the tile's edge pixels of row y0 + r
-            const int im = e / BY, r = e % BY;
-            const int64_t y = y0 + r;
-            if (((im == 0 && H3) || (im == 1 && H4)) && y < M) {
-              const int k = im == 0 ? 3 : 4;
-              // image 3 leaves at x = x0 (f = x0 + z); image 4 at x = x0+XT-1
-              const int64_t f = im == 0 ? x0 + z : x0 + XT - 1 - z + (N - 1);
-              const A* c = (im == 0 ? ex3 : ex4) + ((size_t)sb * BY + r) * PW;
-              if (f >= 0 && f < set.F[k]) emit(img + set.base[k] + y * set.F[k] + f, c[0], FL ? c[PW - 1] : 0.f);
-            }
-            continue;
-          }
-          e -= 2 * BY;
-          if (e < 2 * XT) {  // images 5/6: exit rows
-            const int im = e / XT, col = e % XT;
-            if ((im == 0 && H5) || (im == 1 && H6)) {
-              const int k = im == 0 ? 5 : 6;
-              const int64_t srow = im == 0 ? y0 + z : y0 + BY - 1 - z + (N - 1);
-              const A* c = (im == 0 ? er5 : er6) + ((size_t)sb * XT + col) * PW;
-              if (srow >= 0 && srow < set.S[k] && x0 + col < L)
-                emit(img + set.base[k] + srow * set.F[k] + x0 + col, c[0], FL ? c[PW - 1] : 0.f);
-            }
-            continue;
-          }
-          e -= 2 * XT;
-          {  // images 7/8: per-step diagonal buffers
-            const int im = (H7 && e < kDiag) ? 0 : 1;
-            const int idx = (H7 && e >= kDiag) ? e - kDiag : e;
-            A* cell = dg + ((size_t)(sb * 2 + im) * kDiag + idx) * PW;
-            const int k = 7 + im;
-            const int64_t f = im == 0 ? x0 + y0 + idx : x0 - y0 - (BY - 1) + idx + (M - 1);
-            if (f >= 0 && f < set.F[k]) emit(img + set.base[k] + z * set.F[k] + f, cell[0], FL ? cell[PW - 1] : 0.f);
-            cell[0] = (A)0;
-            if constexpr (FL) cell[1] = 0.f;
+          if (z >= rd.w) {
+            const int64_t base = (int64_t)(((uint64_t)(uint32_t)rd.y << 32) | (uint32_t)rd.x);
+            emit(img + (base + z * (int64_t)rd.z), hv, lv);
           }
         }
       }
@@ -777,7 +866,10 @@ __global__ void __launch_bounds__(NT, 1) k1_project_kernel(K1Params p, const __g
       ++z;
     }
     }
-    if (!aborted) drain(x0, y0, zb - 1);
+    if (!aborted) {
+      drain(x0, y0, zb - 1);
+      __syncthreads();  // roles are rewritten for the next segment
+    }
   }
 
   if (aborted) {
@@ -842,14 +934,12 @@ cudaError_t launch_t(const ProjectArgs& a, cudaStream_t st) {
   p.status = a.status;
 
   auto rnd = [](size_t b) { return (b + 127) & ~size_t(127); };
-  constexpr int kDiag = XT + BY - 1;
+  using X = ExitLayout<BY>;
   size_t smem = rnd(sizeof(uint64_t) * STAGES);
   if (TMA) smem += rnd(sizeof(T) * STAGES * BY * XT);
-  smem += rnd(sizeof(Acc) * PW * 2 * TY * XT);       // slot2
-  smem += 3 * rnd(sizeof(Acc) * PW * 2 * BY);        // slot1, ex3, ex4
-  smem += 2 * rnd(sizeof(Acc) * PW * 2 * TY * XT);   // mb5, mb6
-  smem += 2 * rnd(sizeof(Acc) * PW * 2 * XT);        // er5, er6
-  smem += rnd(sizeof(Acc) * PW * 2 * 2 * kDiag);     // dg
+  smem += 3 * rnd(sizeof(Acc) * PW * 2 * TY * XT);  // slot2, mb5, mb6
+  smem += rnd(sizeof(Acc) * PW * 2 * X::ES);        // exit buffer
+  smem += rnd(sizeof(int4) * X::tasks(P));          // merge roles
 
   auto kern = k1_project_kernel<T, P, TMA>;
   static bool attr_set = false;  // per instantiation
