@@ -35,7 +35,7 @@ L = M = N = 512
 K = 6
 SEED = 3
 WORKLOAD = "mri_like_f32_512x512x512_K6"
-KERNEL_SRC = os.path.join(ROOT, "paper_2012_08099_gb300", "csrc", "k1_project.cu")
+KERNEL_SRC = os.path.join(ROOT, "paper_2012_08099_gb300", "csrc", "k1_project.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k1_project_mri512_f32_k6_traffic.json")
 
 
@@ -48,7 +48,14 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--shape", default=None,
+                    help="L,M,N of a smaller volume of the same recipe (profiling runs)")
+    args = ap.parse_args()
+    if args.shape:
+        global L, M, N, WORKLOAD
+        L, M, N = (int(v) for v in args.shape.split(","))
+        WORKLOAD = f"mri_like_f32_{L}x{M}x{N}_K{K}"
+    return args
 
 
 def dist_info():
@@ -239,7 +246,7 @@ def run_ours(args):
     peak, peak_kind = measured_hbm_peak()
     achieved = algo_bytes / (k1_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic_if_current(),
+                "frac": round(achieved / peak, 4), "traffic": traffic_if_current() if (L, M, N) == (512, 512, 512) else None,
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "kernel": "k1_project (fused projection)", "kernel_ms": round(k1_ms, 5),
                 "pipeline_frac": round(algo_bytes / (ms_step * 1e-3) / 1e9 / peak, 4),
@@ -281,7 +288,8 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "L": L, "M": M, "N": N, "K": K,
                        "moments": nm, "images": dpma.num_images(K),
                        "volume_bytes": int(vol.nbytes), "parallelism": f"replicas{world}",
-                       "l2": "input 537 MB > 129 MB L2 (no flush needed)"},
+                       "l2": f"input {vol.nbytes / 1e6:.0f} MB vs 129 MB L2"
+                             + (" (larger: no flush needed)" if vol.nbytes > 129e6 else "")},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": gpu_launches, "clocks": clk,
         }

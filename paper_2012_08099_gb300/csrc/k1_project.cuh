@@ -151,6 +151,13 @@ __device__ __forceinline__ void ts_acc2(float& h0, float& l0, float v0, float& h
   asm("mov.b64 {%0,%1}, %2;" : "=f"(l0), "=f"(l1) : "l"(Lo));
 }
 
+// (h, l) += (bh, bl): bh enters with TwoSum, bl is added to l (the pair is
+// not renormalised; h + l keeps the sum to about 2^-48 of its magnitude).
+__device__ __forceinline__ void pair_acc(float& h, float& l, float bh, float bl) {
+  ts_acc(h, l, bh);
+  l = __fadd_rn(l, bl);
+}
+
 // The double equal to a float32, from its bits (zero for subnormals, whose
 // magnitude is below 2^-126).
 __device__ __forceinline__ double f32_to_f64_bits(float f) {
@@ -234,18 +241,18 @@ __device__ __forceinline__ void ff_rows_half(const float h[BYT], const float l[B
     const float s1h = up ? h[1] : h[3], s1l = up ? l[1] : l[3];
     const float r0h = __shfl_xor_sync(0xffffffffu, s0h, 8), r0l = __shfl_xor_sync(0xffffffffu, s0l, 8);
     const float r1h = __shfl_xor_sync(0xffffffffu, s1h, 8), r1l = __shfl_xor_sync(0xffffffffu, s1l, 8);
-    ff_add(k0h, k0l, r0h, r0l);
-    ff_add(k1h, k1l, r1h, r1l);
+    pair_acc(k0h, k0l, r0h, r0l);
+    pair_acc(k1h, k1l, r1h, r1l);
     const bool up2 = tx & 4;
     kh = up2 ? k1h : k0h;
     kl = up2 ? k1l : k0l;
     const float sh = up2 ? k0h : k1h, sl = up2 ? k0l : k1l;
     const float qh = __shfl_xor_sync(0xffffffffu, sh, 4), ql = __shfl_xor_sync(0xffffffffu, sl, 4);
-    ff_add(kh, kl, qh, ql);
+    pair_acc(kh, kl, qh, ql);
 #pragma unroll
     for (int m = 2; m >= 1; m >>= 1) {
       const float th = __shfl_xor_sync(0xffffffffu, kh, m), tl = __shfl_xor_sync(0xffffffffu, kl, m);
-      ff_add(kh, kl, th, tl);
+      pair_acc(kh, kl, th, tl);
     }
   } else {
     const bool up = tx & 8;
@@ -253,11 +260,11 @@ __device__ __forceinline__ void ff_rows_half(const float h[BYT], const float l[B
     kl = up ? l[1] : l[0];
     const float sh = up ? h[0] : h[1], sl = up ? l[0] : l[1];
     const float rh = __shfl_xor_sync(0xffffffffu, sh, 8), rl = __shfl_xor_sync(0xffffffffu, sl, 8);
-    ff_add(kh, kl, rh, rl);
+    pair_acc(kh, kl, rh, rl);
 #pragma unroll
     for (int m = 4; m >= 1; m >>= 1) {
       const float th = __shfl_xor_sync(0xffffffffu, kh, m), tl = __shfl_xor_sync(0xffffffffu, kl, m);
-      ff_add(kh, kl, th, tl);
+      pair_acc(kh, kl, th, tl);
     }
   }
   oh = kh;
@@ -585,17 +592,27 @@ __global__ void __launch_bounds__(NT, 1)
 
       // ---- 2. images crossing the slice
       if constexpr (FL) {
+        // register pairs stay fixed for every z phase: images 0, 5, 6 pair
+        // columns (c, c+1) of one window row, images 3, 4 pair rows (r, r+1)
+        // of one window slot
+#pragma unroll
+        for (int r = 0; r < BYT; r += 2)
+#pragma unroll
+          for (int c = 0; c < R; ++c) {
+            if constexpr (H3) {
+              const int q = (c + j) % R;
+              ts_acc2(w3[r][q], w3c[r][q], v[r][c], w3[r + 1][q], w3c[r + 1][q], v[r + 1][c]);
+            }
+            if constexpr (H4) {
+              const int q = (c - j + R) % R;
+              ts_acc2(w4[r][q], w4c[r][q], v[r][c], w4[r + 1][q], w4c[r + 1][q], v[r + 1][c]);
+            }
+          }
 #pragma unroll
         for (int r = 0; r < BYT; ++r)
 #pragma unroll
           for (int c = 0; c < R; c += 2) {
             ts_acc2(a0[r][c], a0c[r][c], v[r][c], a0[r][c + 1], a0c[r][c + 1], v[r][c + 1]);
-            if constexpr (H3)
-              ts_acc2(w3[r][(c + j) % R], w3c[r][(c + j) % R], v[r][c], w3[r][(c + 1 + j) % R],
-                      w3c[r][(c + 1 + j) % R], v[r][c + 1]);
-            if constexpr (H4)
-              ts_acc2(w4[r][(c - j + R) % R], w4c[r][(c - j + R) % R], v[r][c],
-                      w4[r][(c + 1 - j + R) % R], w4c[r][(c + 1 - j + R) % R], v[r][c + 1]);
             if constexpr (H5)
               ts_acc2(w5[(r + j) % BYT][c], w5c[(r + j) % BYT][c], v[r][c], w5[(r + j) % BYT][c + 1],
                       w5c[(r + j) % BYT][c + 1], v[r][c + 1]);
@@ -624,10 +641,16 @@ __global__ void __launch_bounds__(NT, 1)
         for (int c = 0; c < R; ++c) {
           cs[c] = v[0][c];
           csc[c] = 0.f;
+        }
 #pragma unroll
-          for (int r = 1; r < BYT; ++r) {
-            if constexpr (FL) ts_acc(cs[c], csc[c], v[r][c]);
-            else cs[c] += v[r][c];
+        for (int r = 1; r < BYT; ++r) {
+          if constexpr (FL) {
+#pragma unroll
+            for (int c = 0; c < R; c += 2)
+              ts_acc2(cs[c], csc[c], v[r][c], cs[c + 1], csc[c + 1], v[r][c + 1]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < R; ++c) cs[c] += v[r][c];
           }
         }
         A* s2 = slot2 + ((size_t)(sb * TY + ty) * XT + xl) * PW;
@@ -643,10 +666,16 @@ __global__ void __launch_bounds__(NT, 1)
         for (int r = 0; r < BYT; ++r) {
           rs[r] = v[r][0];
           rsc[r] = 0.f;
+        }
 #pragma unroll
-          for (int c = 1; c < R; ++c) {
-            if constexpr (FL) ts_acc(rs[r], rsc[r], v[r][c]);
-            else rs[r] += v[r][c];
+        for (int c = 1; c < R; ++c) {
+          if constexpr (FL) {
+#pragma unroll
+            for (int r = 0; r < BYT; r += 2)
+              ts_acc2(rs[r], rsc[r], v[r][c], rs[r + 1], rsc[r + 1], v[r + 1][c]);
+          } else {
+#pragma unroll
+            for (int r = 0; r < BYT; ++r) rs[r] += v[r][c];
           }
         }
         constexpr int per = 16 / BYT;
@@ -821,19 +850,21 @@ __global__ void __launch_bounds__(NT, 1)
       // ---- 7. merge this step's complete results into the images
       // (a) image 2, one quarter of a column's TY partials per thread
       {
-        A h = 0;
+        const A* e0 = slot2 + ((size_t)(sb * TY + part2 * (TY / 4)) * XT + col2) * PW;
+        A h = e0[0];
         float l = 0.f;
+        if constexpr (FL) l = e0[1];
 #pragma unroll
-        for (int g = part2 * (TY / 4); g < (part2 + 1) * (TY / 4); ++g) {
-          const A* e = slot2 + ((size_t)(sb * TY + g) * XT + col2) * PW;
-          if constexpr (FL) ff_add(h, l, e[0], e[1]);
+        for (int g = 1; g < TY / 4; ++g) {
+          const A* e = e0 + (size_t)g * XT * PW;
+          if constexpr (FL) pair_acc(h, l, e[0], e[1]);
           else h += e[0];
         }
 #pragma unroll
         for (int m = 1; m <= 2; m <<= 1) {
           if constexpr (FL) {
             const float oh = __shfl_xor_sync(0xffffffffu, h, m), ol = __shfl_xor_sync(0xffffffffu, l, m);
-            ff_add(h, l, oh, ol);
+            pair_acc(h, l, oh, ol);
           } else {
             h += __shfl_xor_sync(0xffffffffu, h, m);
           }
