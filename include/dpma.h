@@ -10,7 +10,7 @@
  *   1. project the volume into P = max(3, K+1) discrete line-sum images in one
  *      pass over the voxels, with additions only (Sec. 3.1, Eqs. 4-9);
  *   2. take the 2-D moments of every image (Sec. 1, Eq. 1; Sec. 3.2);
- *   3. combine them linearly into the 3-D moments (Eqs. 10-15, generalised to
+ *   3. combine them linearly into the 3-D moments (Eqs. 10-16, generalised to
  *      any K <= 8 by an exact integer combine matrix per degree).
  *
  * Conventions used by every entry point
@@ -170,7 +170,7 @@ dpma_status dpma_image_moments(const void* images, int64_t L, int64_t M, int64_t
                                void* workspace, size_t workspace_bytes);
 
 /*
- * Step 3 alone (Eqs. 10-15 generalised): 3-D moments from the 2-D moments
+ * Step 3 alone (Eqs. 10-16 generalised): 3-D moments from the 2-D moments
  * of dpma_image_moments (device buffers), enqueued on `stream`.  Integer
  * combines are exact (256-bit accumulation, exact division); a division
  * that leaves a remainder sets DPMA_ERR_INTERNAL in `status` (a device int,

@@ -4,7 +4,7 @@
 // handling around the three device steps:
 //   step 1  launch_project        (Sec. 3.1, Eqs. 4-9)
 //   step 2  launch_image_moments  (Eq. 1 with signed coordinates)
-//   step 3  launch_combine        (Eqs. 10-15 generalised)
+//   step 3  launch_combine        (Eqs. 10-16 generalised)
 #include <cmath>
 #include <cstdio>
 #include <cstring>

@@ -1,5 +1,5 @@
 // Step 3 of the Discrete Projection Moment method: the 3-D moments from the
-// 2-D moments of the projection images (Sec. 3.2, Eqs. 10-15, generalised to
+// 2-D moments of the projection images (Sec. 3.2, Eqs. 10-16, generalised to
 // every degree n <= K with an exact integer combine per degree).
 //
 // Integer volumes: the 2-D moments are exact int128 values; each 3-D moment

@@ -1,5 +1,5 @@
 // Exact combine plan for the final step of the Discrete Projection Moment
-// method (Sec. 3.2, Eqs. 10-15, generalised to any order K <= 8).
+// method (Sec. 3.2, Eqs. 10-16, generalised to any order K <= 8).
 //
 // An image with forms (u, w) has 2-D moments
 //     T_ab = sum_voxels V (u.x)^a (w.x)^b,

@@ -6,7 +6,7 @@
 * the exact combine plan: C A_sel = D I recomputed here in Python integers
   from the image forms, full rank with K+1 directions, the denominators of
   every degree, and -- applied in Python to the oracle's 2-D moments -- it
-  reproduces the oracle's 3-D moments exactly (the paper's Eqs. 10-15 are
+  reproduces the oracle's 3-D moments exactly (the paper's Eqs. 10-16 are
   the K <= 4 special case);
 * argument validation of host-only calls.
 """

@@ -4,8 +4,8 @@
 * a single voxel lands on exactly one pixel per image, where the image's
   two linear forms put it,
 * mass conservation,
-* the paper's identities Eqs. 10-15 between 2-D and 3-D moments, with the
-  labels of Eqs. 14-15 corrected (the printed M112 and M211 formulas are
+* the paper's identities Eqs. 10-16 between 2-D and 3-D moments, with the
+  labels of Eqs. 15-16 corrected (the printed M112 and M211 formulas are
   swapped), checked between two independent oracle functions,
 * the origin shift of the x-z image given in Sec. 5,
 * Eq. 1 on single-pixel images and against exact rationals.
@@ -119,7 +119,7 @@ def test_image_moments_expand_to_3d_moments():
                 assert img_moment(imgs, geo, k, a, n - a, K) == want, (k, a, n - a)
 
 
-def test_paper_identities_eq10_to_eq15():
+def test_paper_identities_eq10_to_eq16():
     vol = synth.uniform_volume((6, 5, 7), np.uint8, seed=3)
     N, M, L = vol.shape
     K = 4
@@ -154,7 +154,7 @@ def test_paper_identities_eq10_to_eq15():
             assert M3(q, 0, p) == zx(p, q)            # Eq. 12
     assert 2 * M3(1, 1, 1) == plus(2, 1) - M3(2, 1, 0) - M3(0, 1, 2)        # Eq. 13
     assert 2 * M3(1, 2, 1) == plus(2, 2) - M3(2, 2, 0) - M3(0, 2, 2)        # Eq. 14
-    # Eq. 15 with the labels corrected:
+    # Eqs. 15-16 with the labels corrected:
     assert 6 * M3(1, 1, 2) == plus(3, 1) + minus(3, 1) - 2 * M3(3, 1, 0)
     assert 6 * M3(2, 1, 1) == plus(3, 1) - minus(3, 1) - 2 * M3(0, 1, 3)
     # ... and the formulas exactly as printed give the other moment:
