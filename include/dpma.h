@@ -179,6 +179,80 @@ dpma_status dpma_image_moments(const void* images, int64_t L, int64_t M, int64_t
 dpma_status dpma_combine(const void* moments2d, dpma_dtype dtype, int K, void* out, void* stream,
                          int* status);
 
+/* ---------------- batches of volumes ---------------- */
+
+/*
+ * One volume of a batch.  `volume` is a device pointer laid out like every
+ * volume of this library; `out_offset` is the byte offset of this volume's
+ * dpma_num_moments(K) moments inside the batch's output buffer (a multiple of
+ * 16; int128 moments for integer volumes, doubles for float32 ones).  Sizes,
+ * element types and orders may differ between the volumes of one batch.
+ */
+typedef struct dpma_volume_desc {
+  const void* volume;
+  int64_t L, M, N;
+  int32_t dtype; /* dpma_dtype */
+  int32_t K;
+  int64_t out_offset;
+} dpma_volume_desc;
+
+/* Opaque batch plan: the task table, its device buffers and the tuned launch. */
+typedef struct dpma_batch dpma_batch;
+
+#define DPMA_BATCH_AUTOTUNE 1 /* time the candidate CTA sizes at creation */
+
+/*
+ * Plans the moments of `count` volumes (the method of Sec. 3 applied to each
+ * volume): validates every descriptor on the host, uploads the task table
+ * and allocates the plan's device buffers (synchronous).  Volumes whose
+ * images fit on chip (integer element types, L <= 256, images within
+ * shared memory) run in one persistent fused launch: projection and 2-D
+ * moments per volume in shared memory, then one batched combine launch.
+ * The others (float32 or larger volumes) run through the single-volume
+ * pipeline, one after another on the same stream.  With
+ * DPMA_BATCH_AUTOTUNE the volumes must already hold their data: the fused
+ * launch is timed at 256 and 512 threads per CTA and the faster is kept.
+ * The descriptors' pointers are kept by the plan until dpma_batch_destroy.
+ * Errors: DPMA_ERR_INVALID_ARG (null pointers, bad descriptor, unknown
+ * flag), DPMA_ERR_OVERFLOW (a volume's moments could leave int128),
+ * DPMA_ERR_OOM, DPMA_ERR_CUDA.
+ */
+dpma_status dpma_batch_create(const dpma_volume_desc* descs, int count, int flags,
+                              dpma_batch** plan);
+
+/*
+ * Enqueues the whole batch on `stream` and returns: device memsets and
+ * kernel launches only (no host synchronisation, no allocation), so the call
+ * can be captured into a CUDA graph and replayed.  `out` is a device buffer
+ * holding every descriptor's out_offset range.  The device status of the run
+ * is read back by dpma_batch_status.  Runs of one plan must not overlap.
+ */
+dpma_status dpma_batch_run(dpma_batch* plan, void* out, void* stream);
+
+/*
+ * Waits for `stream` and returns the status of the plan's last run:
+ * DPMA_OK, DPMA_ERR_INTERNAL (an exact combine left a remainder) or
+ * DPMA_ERR_TIMEOUT (a bounded device wait gave up).
+ */
+dpma_status dpma_batch_status(dpma_batch* plan, void* stream);
+
+/*
+ * Plan facts for tests and tuning: what = 0 volumes in the fused launch,
+ * 1 volumes on the single-volume path, 2 threads per CTA, 3 CTAs of the
+ * fused launch, 4 its dynamic shared memory in bytes; -1 for a bad query.
+ */
+int dpma_batch_info(const dpma_batch* plan, int what);
+
+/* Frees the plan and its device buffers (NULL is accepted). */
+dpma_status dpma_batch_destroy(dpma_batch* plan);
+
+/*
+ * One-shot batch: dpma_batch_create (no autotuning), dpma_batch_run on
+ * `stream`, dpma_batch_status and dpma_batch_destroy.  Synchronous.
+ */
+dpma_status dpma_moments_batched(const dpma_volume_desc* descs, int count, void* out,
+                                 void* stream);
+
 /* ---------------- no device allocation ---------------- */
 
 /*

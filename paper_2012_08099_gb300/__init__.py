@@ -39,6 +39,16 @@ class DpmaError(RuntimeError):
         self.status = status
 
 
+class VolumeDesc(ctypes.Structure):
+    """``dpma_volume_desc`` of include/dpma.h."""
+    _fields_ = [("volume", ctypes.c_void_p), ("L", ctypes.c_int64), ("M", ctypes.c_int64),
+                ("N", ctypes.c_int64), ("dtype", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("out_offset", ctypes.c_int64)]
+
+
+BATCH_AUTOTUNE = 1
+
+
 def lib():
     """The loaded ``libdpma.so`` (raises if it has not been built)."""
     global _lib
@@ -72,6 +82,13 @@ def lib():
                 "dpma_moments_noalloc": (ip, [vp, i64, i64, i64, ip, ip, vp, vp]),
                 "dpma_stage_timing": (ip, [ip]),
                 "dpma_stage_times": (ip, [ctypes.POINTER(ctypes.c_double), P64, ip]),
+                "dpma_batch_create": (ip, [ctypes.POINTER(VolumeDesc), ip, ip,
+                                           ctypes.POINTER(vp)]),
+                "dpma_batch_run": (ip, [vp, vp, vp]),
+                "dpma_batch_status": (ip, [vp, vp]),
+                "dpma_batch_info": (ip, [vp, ip]),
+                "dpma_batch_destroy": (ip, [vp]),
+                "dpma_moments_batched": (ip, [ctypes.POINTER(VolumeDesc), ip, vp, vp]),
             }
             for name, (res, args) in sigs.items():
                 f = getattr(L, name)
@@ -299,3 +316,88 @@ def stage_times(reset: bool = True):
     n = (ctypes.c_int64 * 4)()
     _check(lib().dpma_stage_times(ms, n, 1 if reset else 0))
     return list(ms), list(n)
+
+
+# ------------------------------------------------------------- batches
+
+
+def _descs(volumes, Ks, dtypes=None):
+    """Descriptor array and output layout for CUDA volumes with orders ``Ks``."""
+    n = len(volumes)
+    arr = (VolumeDesc * max(1, n))()
+    offsets, at = [], 0
+    for i, (v, K) in enumerate(zip(volumes, Ks)):
+        dt = dtype_code(v) if dtypes is None or dtypes[i] is None else dtypes[i]
+        L, M, N = _shape(v)
+        arr[i] = VolumeDesc(v.data_ptr(), L, M, N, dt, K, at)
+        offsets.append(at)
+        at += num_moments(K) * 16
+    return arr, offsets, at
+
+
+class Batch:
+    """A planned batch of CUDA volumes (``dpma_batch_*``); ``run`` is graph-capturable."""
+
+    def __init__(self, volumes, Ks, dtypes=None, autotune: bool = False):
+        self.volumes = list(volumes)  # keep the device buffers alive
+        self.Ks = list(Ks)
+        self.dtypes = [dtype_code(v) if dtypes is None or dtypes[i] is None else dtypes[i]
+                       for i, v in enumerate(self.volumes)]
+        self.descs, self.offsets, self.out_bytes = _descs(self.volumes, self.Ks, self.dtypes)
+        h = ctypes.c_void_p()
+        _check(lib().dpma_batch_create(self.descs, len(self.volumes),
+                                       BATCH_AUTOTUNE if autotune else 0, ctypes.byref(h)))
+        self.handle = h
+
+    def info(self, what: int) -> int:
+        return lib().dpma_batch_info(self.handle, what)
+
+    def out_buffer(self, device=None):
+        import torch
+        dev = device if device is not None else self.volumes[0].device
+        return torch.zeros(max(16, self.out_bytes) // 8, dtype=torch.int64, device=dev)
+
+    def run(self, out, stream=None):
+        _check(lib().dpma_batch_run(self.handle, ctypes.c_void_p(out.data_ptr()),
+                                    _stream_ptr(stream)))
+        return out
+
+    def status(self, stream=None):
+        _check(lib().dpma_batch_status(self.handle, _stream_ptr(stream)))
+
+    def values(self, out):
+        """Per volume: exact ints (integer volumes) or float64 numpy (float32 volumes)."""
+        h = out.cpu().numpy()
+        res = []
+        for off, K, dt in zip(self.offsets, self.Ks, self.dtypes):
+            nm = num_moments(K)
+            w = h[off // 8: off // 8 + 2 * nm]
+            res.append(w.view(np.float64)[:nm].copy() if dt == F32 else int128_to_ints(w))
+        return res
+
+    def close(self):
+        if self.handle:
+            lib().dpma_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def moments_batched(volumes, Ks, dtypes=None, stream=None):
+    """One-shot batch (``dpma_moments_batched``): list of per-volume moment values."""
+    import torch
+    descs, offsets, nbytes = _descs(volumes, Ks, dtypes)
+    out = torch.zeros(max(16, nbytes) // 8, dtype=torch.int64, device=volumes[0].device)
+    _check(lib().dpma_moments_batched(descs, len(volumes), ctypes.c_void_p(out.data_ptr()),
+                                      _stream_ptr(stream)))
+    h = out.cpu().numpy()
+    res = []
+    for i, (off, K) in enumerate(zip(offsets, Ks)):
+        nm = num_moments(K)
+        w = h[off // 8: off // 8 + 2 * nm]
+        res.append(w.view(np.float64)[:nm].copy() if descs[i].dtype == F32 else int128_to_ints(w))
+    return res

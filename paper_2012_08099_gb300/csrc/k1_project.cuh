@@ -64,9 +64,13 @@ template <typename T, int P> struct TileCfg {
   static constexpr bool FL = std::is_same<T, float>::value;
   static constexpr int BYT = (FL && P >= 6) ? 2 : 4;
   static constexpr int BY = BYT * TY;
-  // ring depth: about 64 KB of slices in flight per CTA, 4 to 16 stages
+  // resident CTAs per SM: integer state fits 128 registers per thread, so
+  // two CTAs share an SM; float state (hi, lo pairs) needs one CTA
+  static constexpr int MINB = FL ? 1 : 2;
+  // ring depth: about 64 KB of slices in flight per SM, 4 to 16 stages
   static constexpr int SLICE = BY * XT * (int)sizeof(T);
-  static constexpr int STAGES = SLICE >= 16384 ? 4 : (SLICE >= 8192 ? 8 : 16);
+  static constexpr int FLIGHT = 65536 / MINB;
+  static constexpr int STAGES = SLICE * 4 >= FLIGHT ? 4 : (SLICE * 8 >= FLIGHT ? 8 : 16);
   static_assert(R % BYT == 0, "window rotations share the unroll period R");
 };
 
@@ -75,6 +79,7 @@ struct K1Params {
   int64_t L, M, N;
   int64_t nbands, nxt;
   int64_t units;  // nxt * nbands * N
+  int64_t cpt;    // CTAs per x-tile (grid = nxt * cpt), or 0: contiguous ranges
   ImageSet set;
   void* images;
   int* status;
@@ -314,7 +319,7 @@ template <int BY> struct ExitLayout {
 };
 
 template <typename T, int P, bool TMA>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
     k1_project_kernel(K1Params p, const __grid_constant__ CUtensorMap vmap) {
   using C = TileCfg<T, P>;
   constexpr bool FL = C::FL;
@@ -353,8 +358,20 @@ __global__ void __launch_bounds__(NT, 1)
   const bool vec_global =
       (L % R) == 0 && ((reinterpret_cast<uintptr_t>(p.vol) % (R * sizeof(T))) == 0);
 
-  const int64_t ub = p.units * (int64_t)blockIdx.x / gridDim.x;
-  const int64_t ue = p.units * (int64_t)(blockIdx.x + 1) / gridDim.x;
+  // Units are numbered (tile, band, z), z fastest.  With cpt > 0, CTA b
+  // takes tile b % nxt and the (b / nxt)-th of cpt equal ranges of that
+  // tile's (band, z) units, so the nxt CTAs of consecutive indexes stream
+  // the same rows at the same z and together read whole rows of the volume.
+  int64_t ub, ue;
+  if (p.cpt > 0) {
+    const int64_t tile = blockIdx.x % p.nxt, c = blockIdx.x / p.nxt;
+    const int64_t W = p.nbands * p.N;
+    ub = tile * W + W * c / p.cpt;
+    ue = tile * W + W * (c + 1) / p.cpt;
+  } else {
+    ub = p.units * (int64_t)blockIdx.x / gridDim.x;
+    ue = p.units * (int64_t)(blockIdx.x + 1) / gridDim.x;
+  }
 
   for (int i = tid; i < 2 * X::ES * PW; i += NT) xb[i] = (A)0;
   if constexpr (TMA) {
@@ -994,10 +1011,22 @@ cudaError_t launch_t(const ProjectArgs& a, cudaStream_t st) {
     if (dev < 64) { cached_sms[dev] = sms; cached_per_sm[dev] = per_sm; }
   }
   // at least ~8 z-steps per CTA so segment drains stay a small overhead
-  int64_t grid = (int64_t)sms * per_sm;
-  const int64_t by_work = (p.units + 7) / 8;
-  if (grid > by_work) grid = by_work;
-  if (grid < 1) grid = 1;
+  const int64_t gmax = (int64_t)sms * per_sm;
+  int64_t grid;
+  if (p.nxt <= gmax) {  // tile-major ranges, nxt CTAs per (band, z) range
+    const int64_t W = p.nbands * a.N;
+    int64_t cpt = gmax / p.nxt;
+    if (cpt > (W + 7) / 8) cpt = (W + 7) / 8;
+    if (cpt < 1) cpt = 1;
+    p.cpt = cpt;
+    grid = p.nxt * cpt;
+  } else {
+    p.cpt = 0;
+    grid = gmax;
+    const int64_t by_work = (p.units + 7) / 8;
+    if (grid > by_work) grid = by_work;
+    if (grid < 1) grid = 1;
+  }
   CUtensorMap vmap;
   std::memset(&vmap, 0, sizeof(vmap));
   if (TMA) {

@@ -176,3 +176,29 @@ def test_status_strings(lib):
         assert lib.dpma_status_string(s)
     assert lib.dpma_combine_plan(3, 4, None, None, None, None, None) == 1
     assert b"0 <= n <= K" in lib.dpma_last_error()
+
+
+def test_batch_arguments_checked_on_the_host(lib):
+    """dpma_batch_create validates every descriptor before touching a device."""
+    import paper_2012_08099_gb300 as d
+    h = ctypes.c_void_p()
+    assert lib.dpma_batch_create(None, 1, 0, ctypes.byref(h)) == 1
+    assert lib.dpma_batch_create(None, -1, 0, ctypes.byref(h)) == 1
+
+    def one(**kw):
+        f = dict(volume=0x1000, L=8, M=8, N=8, dtype=d.U8, K=3, out_offset=0)
+        f.update(kw)
+        arr = (d.VolumeDesc * 1)(d.VolumeDesc(**f))
+        return lib.dpma_batch_create(arr, 1, 0, ctypes.byref(h))
+
+    assert one(volume=None) == 1
+    assert one(out_offset=8) == 1
+    assert one(out_offset=-16) == 1
+    assert one(L=0) == 1
+    assert one(K=9) == 1
+    assert one(dtype=5) == 1
+    assert one(L=65536, M=65536, N=65536, dtype=d.U16, K=8) == 2
+    arr = (d.VolumeDesc * 1)(d.VolumeDesc(0x1000, 8, 8, 8, d.U8, 3, 0))
+    assert lib.dpma_batch_create(arr, 1, 4, ctypes.byref(h)) == 1  # unknown flag
+    assert lib.dpma_batch_info(None, 0) == -1
+    assert lib.dpma_batch_destroy(None) == 0

@@ -1,0 +1,177 @@
+"""GPU parity of the batched path (``dpma_batch_*``, ``dpma_moments_batched``).
+
+Every volume of a batch must give exactly what the single-volume path gives
+(integer volumes bit for bit, float volumes identical because they take that
+very path), a sample must match the oracle, a run captured in a CUDA graph
+must replay with new volume contents, and the batch of 4096 binary ROI masks
+at K = 4 must be exact for every ROI.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2012_08099_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dpma():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2012_08099_gb300 as d
+    d.lib()
+    return d
+
+
+def dev(vol):
+    import paper_2012_08099_gb300 as d
+    if vol.dtype == np.uint16:
+        return torch.from_numpy(vol.view(np.int16)).cuda(), d.U16
+    if vol.dtype == np.uint8:
+        return torch.from_numpy(vol).cuda(), d.U8
+    return torch.from_numpy(vol).cuda(), d.F32
+
+
+def mixed_batch():
+    """ROI masks plus odd sizes, orders 0..8, 16- and 32-bit pixels, and volumes
+    that take the single-volume path (float32, L > 256)."""
+    vols, Ks = [], []
+    for v in synth.roi_batch(40, seed=11).volumes:
+        vols.append(v)
+        Ks.append(4)
+    cases = [
+        ((20, 30, 40), np.uint16, 3), ((33, 17, 65), np.uint16, 6), ((9, 40, 100), np.uint16, 8),
+        ((1, 1, 1), np.uint16, 0), ((2, 3, 1), np.uint8, 2), ((5, 7, 256), np.uint16, 5),
+        ((12, 13, 14), np.uint8, 7), ((30, 20, 10), np.uint8, 8), ((64, 64, 64), np.uint8, 4),
+        ((300, 4, 4), np.uint8, 4), ((4, 4, 300), np.uint16, 4), ((10, 11, 12), np.float32, 6),
+        ((3, 1, 257), np.uint8, 3), ((1, 96, 1), np.uint8, 1),
+    ]
+    for i, (shape, dt, K) in enumerate(cases):
+        vols.append(synth.uniform_volume(shape, dt, seed=100 + i))
+        Ks.append(K)
+    return vols, Ks
+
+
+def single(dpma, t, K, dt):
+    return dpma.moments_values(t, K, dt)
+
+
+def same(a, b):
+    if isinstance(a, np.ndarray):
+        return np.array_equal(a, b)
+    return a == b
+
+
+def test_batched_matches_single_volume(dpma):
+    vols, Ks = mixed_batch()
+    tv = [dev(v) for v in vols]
+    b = dpma.Batch([t for t, _ in tv], Ks, [d for _, d in tv])
+    assert b.info(1) == 3                  # float32 and the two volumes with L > 256
+    assert b.info(0) == len(vols) - 3      # every other volume is fused
+    out = b.out_buffer()
+    b.run(out)
+    b.status()
+    got = b.values(out)
+    for (t, d), K, g in zip(tv, Ks, got):
+        assert same(g, single(dpma, t, K, d)), (tuple(t.shape), K)
+
+
+def test_batched_matches_oracle(dpma):
+    vols, Ks = mixed_batch()
+    pick = [0, 7, 39, 40, 41, 42, 45, 46, 47, 48]
+    vs = [vols[i] for i in pick]
+    ks = [Ks[i] for i in pick]
+    tv = [dev(v) for v in vs]
+    got = dpma.moments_batched([t for t, _ in tv], ks, [d for _, d in tv])
+    for v, K, g in zip(vs, ks, got):
+        assert g == oracle.moments(v, K), (v.shape, K)
+
+
+def test_batch_run_twice_and_reuse(dpma):
+    vols, Ks = mixed_batch()
+    tv = [dev(v) for v in vols[:20]]
+    b = dpma.Batch([t for t, _ in tv], Ks[:20], [d for _, d in tv])
+    out1, out2 = b.out_buffer(), b.out_buffer()
+    b.run(out1)
+    b.run(out2)
+    b.status()
+    assert torch.equal(out1, out2)
+
+
+def test_graph_capture_and_replay(dpma):
+    vols, Ks = mixed_batch()
+    sel = list(range(0, 40, 5)) + [40, 41, 42, 51]   # fused ROIs, u16 volumes, one float
+    tv = [dev(vols[i]) for i in sel]
+    ks = [Ks[i] for i in sel]
+    b = dpma.Batch([t for t, _ in tv], ks, [d for _, d in tv])
+    out = b.out_buffer()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.run(out)                     # warm: kernel attributes and plans set up
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.run(out)
+    # new contents in the same buffers, then replay
+    for j, (t, d) in enumerate(tv):
+        v = vols[sel[j]]
+        fresh = synth.uniform_volume(v.shape, v.dtype, seed=900 + j)
+        if d == dpma.U8 and v.max() <= 1:
+            fresh = (fresh > 127).astype(np.uint8)
+        t.copy_(dev(fresh)[0])
+    out.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    got = b.values(out)
+    for (t, d), K, gv in zip(tv, ks, got):
+        assert same(gv, single(dpma, t, K, d)), (tuple(t.shape), K)
+
+
+def test_autotune_keeps_results(dpma):
+    vols, Ks = mixed_batch()
+    tv = [dev(v) for v in vols[:40]]
+    b = dpma.Batch([t for t, _ in tv], Ks[:40], [d for _, d in tv], autotune=True)
+    assert b.info(2) in (256, 512)
+    out = b.out_buffer()
+    b.run(out)
+    b.status()
+    for (t, d), K, g in zip(tv, Ks[:40], b.values(out)):
+        assert g == single(dpma, t, K, d)
+
+
+def test_config_4096_roi_masks_k4(dpma):
+    """4096 binary ROI masks (sizes log-uniform 8..96), K = 4, one fused launch."""
+    rb = synth.roi_batch(4096, seed=4)
+    tv = [dev(v) for v in rb.volumes]
+    b = dpma.Batch([t for t, _ in tv], [4] * len(tv), [d for _, d in tv])
+    assert b.info(0) == 4096 and b.info(1) == 0
+    out = b.out_buffer()
+    b.run(out)
+    b.status()
+    got = b.values(out)
+    # every ROI against the single-volume path would take 4096 launches of
+    # each kernel; check every 16th there and all of them against a host
+    # recomputation of the two cheapest exact invariants: mass and centroid sums
+    for i in range(0, 4096, 16):
+        t, d = tv[i]
+        assert got[i] == single(dpma, t, 4, d), i
+    for i, v in enumerate(rb.volumes):
+        N, M, L = v.shape
+        w = v.astype(np.int64)
+        assert got[i][0] == int(w.sum())
+        assert got[i][1] == int((w.sum(axis=(0, 1)) * np.arange(L)).sum())
+        assert got[i][2] == int((w.sum(axis=(0, 2)) * np.arange(M)).sum())
+        assert got[i][3] == int((w.sum(axis=(1, 2)) * np.arange(N)).sum())
+
+
+def test_batch_rejects_bad_descriptors(dpma):
+    t, d = dev(synth.uniform_volume((4, 4, 4), np.uint8, seed=1))
+    with pytest.raises(dpma.DpmaError) as e:
+        dpma.Batch([t], [9], [d])
+    assert e.value.status == 1
+    with pytest.raises(dpma.DpmaError) as e:
+        dpma.Batch([t], [3], [7])
+    assert e.value.status == 1
