@@ -253,6 +253,82 @@ dpma_status dpma_batch_destroy(dpma_batch* plan);
 dpma_status dpma_moments_batched(const dpma_volume_desc* descs, int count, void* out,
                                  void* stream);
 
+/* ---------------- serving ---------------- */
+
+/*
+ * Continuous-batching server for a stream of moment requests (each request:
+ * the method of Sec. 3 on one volume).  Zero fields take the defaults.
+ *   device_bytes  device memory the server holds for requests in flight
+ *                 (default: a quarter of the free memory at creation);
+ *   max_inflight  requests on the device at once (default 64);
+ *   streams       CUDA streams the launches are spread over (default 4);
+ *   max_group     most small volumes fused into one launch (default 256);
+ *   max_pending   queued requests before submit refuses (default 4096).
+ */
+typedef struct dpma_server_config {
+  int64_t device_bytes;
+  int32_t max_inflight;
+  int32_t streams;
+  int32_t max_group;
+  int32_t max_pending;
+} dpma_server_config;
+
+/* Counters since creation (or the last reset); latencies are submit-to-done. */
+typedef struct dpma_server_counters {
+  int64_t submitted, completed, failed, rejected, pending, inflight, launches;
+  int64_t device_bytes_peak;
+  double p50_ms, p99_ms, mean_ms, max_ms;
+  double volumes_per_s, voxels_per_s; /* completed / (last done - first submit) */
+} dpma_server_counters;
+
+typedef struct dpma_server dpma_server;
+
+/*
+ * Creates a server on the current device: allocates its device arena,
+ * control blocks and streams, makes every combine plan resident and starts
+ * its scheduler thread.  A scheduler admits queued requests in arrival order
+ * whenever a slot and enough arena memory are free and launches them at once
+ * (small integer volumes fused into one launch, the rest through the
+ * single-volume pipeline), so requests that arrive while others run are
+ * admitted as resources free up and their work overlaps on the device.
+ * Errors: DPMA_ERR_INVALID_ARG, DPMA_ERR_OOM, DPMA_ERR_CUDA.
+ */
+dpma_status dpma_server_create(const dpma_server_config* cfg, dpma_server** server);
+
+/*
+ * Queues one request.  desc->volume is a HOST pointer; the volume is copied
+ * before the call returns (desc->out_offset is ignored).  *ticket identifies
+ * the request for dpma_server_wait / dpma_server_poll.  Thread-safe.
+ * Errors: DPMA_ERR_INVALID_ARG / DPMA_ERR_OVERFLOW (descriptor), 
+ * DPMA_ERR_REJECTED (queue full, or more device memory than the server
+ * holds), DPMA_ERR_OOM (pinned host memory).
+ */
+dpma_status dpma_server_submit(dpma_server* server, const dpma_volume_desc* desc,
+                               uint64_t* ticket);
+
+/*
+ * Waits up to timeout_ms (< 0: no limit, 0: just check) for a request; on
+ * success copies its dpma_num_moments(K) moments to host_out (int128 or
+ * double; may be NULL) and releases the ticket.  DPMA_ERR_TIMEOUT: not
+ * finished yet (the ticket stays valid); any other error releases the ticket
+ * and reports the request's failure.  Thread-safe.
+ */
+dpma_status dpma_server_wait(dpma_server* server, uint64_t ticket, int64_t timeout_ms,
+                             void* host_out);
+
+/* 1: finished, 0: queued or running, -1: unknown ticket. */
+int dpma_server_poll(dpma_server* server, uint64_t ticket);
+
+/* Copies the counters; reset != 0 starts new ones. */
+dpma_status dpma_server_stats(dpma_server* server, dpma_server_counters* out, int reset);
+
+/*
+ * Stops admitting, waits for the requests in flight, fails the queued ones
+ * (DPMA_ERR_REJECTED) and frees the server.  No thread may use the server
+ * during or after the call.  NULL is accepted.
+ */
+dpma_status dpma_server_destroy(dpma_server* server);
+
 /* ---------------- no device allocation ---------------- */
 
 /*

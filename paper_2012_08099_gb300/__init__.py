@@ -49,6 +49,22 @@ class VolumeDesc(ctypes.Structure):
 BATCH_AUTOTUNE = 1
 
 
+class ServerConfig(ctypes.Structure):
+    """``dpma_server_config`` of include/dpma.h (zero fields take the defaults)."""
+    _fields_ = [("device_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
+                ("streams", ctypes.c_int32), ("max_group", ctypes.c_int32),
+                ("max_pending", ctypes.c_int32)]
+
+
+class ServerCounters(ctypes.Structure):
+    """``dpma_server_counters`` of include/dpma.h."""
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "rejected",
+                                              "pending", "inflight", "launches",
+                                              "device_bytes_peak")] + \
+               [(n, ctypes.c_double) for n in ("p50_ms", "p99_ms", "mean_ms", "max_ms",
+                                               "volumes_per_s", "voxels_per_s")]
+
+
 def lib():
     """The loaded ``libdpma.so`` (raises if it has not been built)."""
     global _lib
@@ -89,6 +105,13 @@ def lib():
                 "dpma_batch_info": (ip, [vp, ip]),
                 "dpma_batch_destroy": (ip, [vp]),
                 "dpma_moments_batched": (ip, [ctypes.POINTER(VolumeDesc), ip, vp, vp]),
+                "dpma_server_create": (ip, [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]),
+                "dpma_server_submit": (ip, [vp, ctypes.POINTER(VolumeDesc),
+                                            ctypes.POINTER(ctypes.c_uint64)]),
+                "dpma_server_wait": (ip, [vp, ctypes.c_uint64, i64, vp]),
+                "dpma_server_poll": (ip, [vp, ctypes.c_uint64]),
+                "dpma_server_stats": (ip, [vp, ctypes.POINTER(ServerCounters), ip]),
+                "dpma_server_destroy": (ip, [vp]),
             }
             for name, (res, args) in sigs.items():
                 f = getattr(L, name)
@@ -401,3 +424,67 @@ def moments_batched(volumes, Ks, dtypes=None, stream=None):
         w = h[off // 8: off // 8 + 2 * nm]
         res.append(w.view(np.float64)[:nm].copy() if descs[i].dtype == F32 else int128_to_ints(w))
     return res
+
+
+# -------------------------------------------------------------- serving
+
+
+class Server:
+    """Continuous-batching moment server (``dpma_server_*``) on the current device.
+
+    ``submit`` takes a host numpy volume (copied before it returns) and its
+    order K and gives a ticket; ``wait`` returns the moments (exact ints for
+    integer volumes, float64 numpy for float32 ones).
+    """
+
+    def __init__(self, device_bytes=0, max_inflight=0, streams=0, max_group=0, max_pending=0):
+        cfg = ServerConfig(device_bytes, max_inflight, streams, max_group, max_pending)
+        h = ctypes.c_void_p()
+        _check(lib().dpma_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+        self._meta = {}
+
+    def submit(self, volume: np.ndarray, K: int, dtype: int | None = None) -> int:
+        vol = np.ascontiguousarray(volume)
+        dt = dtype_code(vol) if dtype is None else dtype
+        N, M, L = vol.shape
+        d = VolumeDesc(vol.ctypes.data, L, M, N, dt, K, 0)
+        t = ctypes.c_uint64()
+        _check(lib().dpma_server_submit(self.handle, ctypes.byref(d), ctypes.byref(t)))
+        self._meta[t.value] = (K, dt)
+        return t.value
+
+    def poll(self, ticket: int) -> int:
+        return lib().dpma_server_poll(self.handle, ticket)
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        K, dt = self._meta[ticket]
+        nm = num_moments(K)
+        out = np.empty((nm, 2) if dt != F32 else (nm,), dtype=np.int64 if dt != F32 else np.float64)
+        rc = lib().dpma_server_wait(self.handle, ticket, timeout_ms, ctypes.c_void_p(out.ctypes.data))
+        if rc != 5:
+            self._meta.pop(ticket, None)
+        _check(rc)
+        return out if dt == F32 else int128_to_ints(out)
+
+    def stats(self, reset: bool = False) -> dict:
+        c = ServerCounters()
+        _check(lib().dpma_server_stats(self.handle, ctypes.byref(c), 1 if reset else 0))
+        return {n: getattr(c, n) for n, _ in ServerCounters._fields_}
+
+    def close(self):
+        if self.handle:
+            lib().dpma_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "../../include/dpma.h"
+#include "batch_internal.cuh"
 #include "dpma_internal.cuh"
 
 namespace dpma {
@@ -38,6 +39,7 @@ void set_last_error(const char* msg);
 }  // namespace dpma
 
 using namespace dpma;
+using dpma::batch::BTask;
 
 namespace {
 
@@ -47,17 +49,6 @@ constexpr int kPartBytes = kMaxWarps * kMax2D * 16;  // per-warp 2-D moment part
 constexpr int kSmemLimit = 227 * 1024;
 constexpr int kStatusInternal = 7;
 
-struct BTask {
-  const void* vol;
-  int L, M, N;
-  int dtype, K, P;
-  int wide;   // 1: 32-bit pixels, 0: 16-bit pixels
-  int r64;    // 1: row power sums fit int64
-  int words;  // 32-bit words of shared memory the images take
-  int img_off[kMaxImages];  // first pixel of each image (even, in pixel units)
-  int64_t t_off;            // first 2-D moment of this volume in T (int128 units)
-  int64_t out_off;          // byte offset of this volume's moments in `out`
-};
 
 struct FusedParams {
   const BTask* tasks;
@@ -388,7 +379,7 @@ __global__ void merge_status_kernel(const int* src, int* dst) {
   if (*src) atomicMax(dst, *src);
 }
 
-// ---------------------------------------------------------------- host plan
+// ---------------------------------------------------------------- host side
 
 dpma_status bfail(dpma_status s, const std::string& m) {
   set_last_error(m.c_str());
@@ -398,27 +389,185 @@ dpma_status bfail(dpma_status s, const std::string& m) {
 // Upper bound on the voxels one pixel sums (the longest line of any image).
 int64_t longest_line(int64_t L, int64_t M, int64_t N) { return std::max({N, L, M}); }
 
+template <int NT>
+cudaError_t set_smem(size_t smem) {
+  return cudaFuncSetAttribute(batch_fused_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
+}
+
+struct DevPlans {
+  int64_t* words = nullptr;
+  int off[kMaxK + 1][kMaxK + 1] = {};
+};
+std::mutex g_plans_mu;
+std::vector<DevPlans> g_plans;  // per device
+
+cudaError_t plans_for_device(const DevPlans** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_plans_mu);
+  if ((int)g_plans.size() <= dev) g_plans.resize(dev + 1);
+  DevPlans& dp = g_plans[dev];
+  if (!dp.words) {
+    std::vector<int64_t> words;
+    for (int K = 0; K <= kMaxK; ++K) {
+      std::vector<int64_t> w(8192);
+      int off[kMaxK + 1];
+      const size_t n = pack_combine_plan(K, w.data(), w.size(), off);
+      if (n == 0) return cudaErrorInvalidValue;
+      for (int d = 0; d <= kMaxK; ++d) dp.off[K][d] = (int)words.size() + off[d];
+      words.insert(words.end(), w.begin(), w.begin() + n);
+    }
+    int64_t* dw = nullptr;
+    e = cudaMalloc(&dw, sizeof(int64_t) * words.size());
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(dw, words.data(), sizeof(int64_t) * words.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(dw); return e; }
+    dp.words = dw;
+  }
+  *out = &dp;
+  return cudaSuccess;
+}
+
 }  // namespace
+
+namespace dpma {
+namespace batch {
+
+void classify(const dpma_volume_desc* descs, int count, Classified* c) {
+  *c = Classified{};
+  for (int i = 0; i < count; ++i) {
+    const dpma_volume_desc& d = descs[i];
+    const int P = num_images(d.K);
+    bool fused = d.dtype != DPMA_F32 && d.L <= 32 * kMaxXSlots;
+    BTask t{};
+    if (fused) {
+      const double vmax = d.dtype == DPMA_U8 ? 255.0 : 65535.0;
+      const int64_t line = longest_line(d.L, d.M, d.N);
+      t.wide = vmax * (double)line >= 65536.0 ? 1 : 0;
+      int64_t pix = 0, maxF = 1;
+      for (int k = 0; k < P; ++k) {
+        ImageGeom g;
+        image_geom(k, d.L, d.M, d.N, &g);
+        t.img_off[k] = (int)std::min<int64_t>(pix, 1 << 30);
+        pix += (g.S * g.F + 1) & ~int64_t(1);  // even: 16-bit pixels pair up in words
+        maxF = std::max(maxF, std::max(g.F, g.S));
+      }
+      const int64_t words = t.wide ? pix : pix / 2;
+      if (pix > (1ll << 30) || (size_t)words * 4 + kPartBytes > (size_t)kSmemLimit) fused = false;
+      if (fused) {
+        t.vol = d.volume;
+        t.L = (int)d.L; t.M = (int)d.M; t.N = (int)d.N;
+        t.dtype = d.dtype; t.K = d.K; t.P = P;
+        t.words = (int)words;
+        // a row power sum is at most (vmax * line) * maxF^K * maxF
+        const double bits = std::log2(vmax * (double)line + 1) + d.K * std::log2((double)maxF + 1) +
+                            std::log2((double)maxF + 1);
+        t.r64 = bits < 62.0 ? 1 : 0;
+        t.t_off = c->t_total;
+        t.out_off = d.out_offset;
+        c->t_total += (int64_t)P * num_2d(d.K);
+        c->tasks.push_back(t);
+        c->fused_index.push_back(i);
+        c->max_words = std::max(c->max_words, (size_t)words);
+      }
+    }
+    if (!fused) c->single.push_back(i);
+  }
+}
+
+std::vector<int> lpt_order(const std::vector<BTask>& tasks) {
+  std::vector<int> order(tasks.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const BTask &a = tasks[x], &c = tasks[y];
+    return (int64_t)a.L * a.M * a.N > (int64_t)c.L * c.M * c.N;
+  });
+  return order;
+}
+
+size_t fused_smem(size_t max_words) { return (size_t)kPartBytes + max_words * 4; }
+
+int fused_grid(size_t smem, int threads, int ntasks) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e;
+  if (threads == 512) {
+    set_smem<512>(smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_fused_kernel<512>, 512, smem);
+  } else {
+    set_smem<256>(smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_fused_kernel<256>, 256, smem);
+  }
+  if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+  return std::max(1, std::min(sms * per_sm, ntasks));
+}
+
+cudaError_t prepare_plans() {
+  const DevPlans* dp = nullptr;
+  return plans_for_device(&dp);
+}
+
+cudaError_t enqueue_fused(const BTask* d_tasks, const int* d_order, int n, int* d_counter,
+                          i128* d_T, size_t smem, int threads, int grid, void* out,
+                          int* d_status, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const DevPlans* dp = nullptr;
+  cudaError_t e = plans_for_device(&dp);
+  if (e != cudaSuccess) return e;
+  FusedParams p{};
+  p.tasks = d_tasks;
+  p.order = d_order;
+  p.ntasks = n;
+  p.counter = d_counter;
+  p.T = d_T;
+  if (threads == 512) {
+    e = set_smem<512>(smem);
+    if (e != cudaSuccess) return e;
+    batch_fused_kernel<512><<<grid, 512, smem, st>>>(p);
+  } else {
+    e = set_smem<256>(smem);
+    if (e != cudaSuccess) return e;
+    batch_fused_kernel<256><<<grid, 256, smem, st>>>(p);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  BCombParams cp{};
+  cp.tasks = d_tasks;
+  cp.ntasks = n;
+  cp.plans = dp->words;
+  std::memcpy(cp.off, dp->off, sizeof(cp.off));
+  cp.T = d_T;
+  cp.out = static_cast<unsigned char*>(out);
+  cp.status = d_status;
+  const int64_t nt = 128, total = (int64_t)n * 165;
+  batch_combine_kernel<<<(unsigned)((total + nt - 1) / nt), (unsigned)nt, 0, st>>>(cp);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_merge_status(const int* src, int* dst, cudaStream_t st) {
+  merge_status_kernel<<<1, 1, 0, st>>>(src, dst);
+  return cudaGetLastError();
+}
+
+}  // namespace batch
+}  // namespace dpma
 
 struct dpma_batch {
   int device = 0;
-  int count = 0;
   std::vector<dpma_volume_desc> descs;
-  // fused part
-  std::vector<BTask> tasks;         // host copy
+  batch::Classified cls;
   BTask* d_tasks = nullptr;
   int* d_order = nullptr;
   int* d_counter = nullptr;
   int* d_status = nullptr;
   i128* d_T = nullptr;
-  int64_t* d_plans = nullptr;
-  int plan_off[kMaxK + 1][kMaxK + 1] = {};
   size_t smem = 0;
   int threads = 512;
   int grid = 0;
-  // volumes that run through the single-volume pipeline
-  std::vector<int> single;
-  void* d_ws = nullptr;
+  void* d_ws = nullptr;  // workspace of the single-volume path
   size_t ws_bytes = 0;
 };
 
@@ -431,84 +580,66 @@ void free_plan(dpma_batch* b) {
   cudaFree(b->d_counter);
   cudaFree(b->d_status);
   cudaFree(b->d_T);
-  cudaFree(b->d_plans);
   cudaFree(b->d_ws);
   delete b;
 }
 
-template <int NT>
-cudaError_t launch_fused(dpma_batch* b, cudaStream_t st) {
-  auto kern = batch_fused_kernel<NT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)b->smem);
-  if (e != cudaSuccess) return e;
-  FusedParams p{};
-  p.tasks = b->d_tasks;
-  p.order = b->d_order;
-  p.ntasks = (int)b->tasks.size();
-  p.counter = b->d_counter;
-  p.T = b->d_T;
-  kern<<<b->grid, NT, b->smem, st>>>(p);
-  return cudaGetLastError();
-}
-
-int grid_for(dpma_batch* b, int nt) {
-  int dev = b->device, sms = 0, per_sm = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e;
-  if (nt == 512) {
-    cudaFuncSetAttribute(batch_fused_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)b->smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_fused_kernel<512>, 512, b->smem);
-  } else {
-    cudaFuncSetAttribute(batch_fused_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)b->smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_fused_kernel<256>, 256, b->smem);
-  }
-  if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-  const int g = sms * per_sm;
-  return std::max(1, std::min(g, (int)b->tasks.size()));
-}
-
-dpma_status enqueue_batch(dpma_batch* b, void* out, cudaStream_t st) {
+dpma_status enqueue_batch(dpma_batch* b, void* out, cudaStream_t st, bool singles = true) {
   unsigned char* o = static_cast<unsigned char*>(out);
   cudaError_t e = cudaMemsetAsync(b->d_status, 0, sizeof(int), st);
   if (e != cudaSuccess) return bfail(DPMA_ERR_CUDA, std::string("clear status: ") + cudaGetErrorString(e));
-  if (!b->tasks.empty()) {
+  const int n = (int)b->cls.tasks.size();
+  if (n > 0) {
     e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = b->threads == 512 ? launch_fused<512>(b, st) : launch_fused<256>(b, st);
+    if (e == cudaSuccess)
+      e = batch::enqueue_fused(b->d_tasks, b->d_order, n, b->d_counter, b->d_T, b->smem,
+                               b->threads, b->grid, out, b->d_status, st);
     if (e != cudaSuccess)
-      return bfail(DPMA_ERR_CUDA, std::string("batched projection kernel: ") + cudaGetErrorString(e));
-    BCombParams cp{};
-    cp.tasks = b->d_tasks;
-    cp.ntasks = (int)b->tasks.size();
-    cp.plans = b->d_plans;
-    std::memcpy(cp.off, b->plan_off, sizeof(cp.off));
-    cp.T = b->d_T;
-    cp.out = o;
-    cp.status = b->d_status;
-    const int64_t threads = 128, total = (int64_t)cp.ntasks * 165;
-    batch_combine_kernel<<<(unsigned)((total + threads - 1) / threads), (unsigned)threads, 0, st>>>(cp);
-    e = cudaGetLastError();
-    if (e != cudaSuccess)
-      return bfail(DPMA_ERR_CUDA, std::string("batched combine kernel: ") + cudaGetErrorString(e));
+      return bfail(DPMA_ERR_CUDA, std::string("batched kernels: ") + cudaGetErrorString(e));
   }
-  for (int i : b->single) {
+  if (!singles) return DPMA_OK;
+  for (int i : b->cls.single) {
     const dpma_volume_desc& d = b->descs[i];
     dpma_status s = dpma_moments_async(d.volume, d.L, d.M, d.N, (dpma_dtype)d.dtype, d.K,
                                        o + d.out_offset, st, b->d_ws, b->ws_bytes);
     if (s != DPMA_OK) return s;
     // a single-volume layout keeps its status word in its last 256 bytes
     const size_t total = dpma_workspace_size(d.L, d.M, d.N, (dpma_dtype)d.dtype, d.K);
-    const int* ws_status = reinterpret_cast<const int*>(static_cast<unsigned char*>(b->d_ws) + total - 256);
-    merge_status_kernel<<<1, 1, 0, st>>>(ws_status, b->d_status);
-    e = cudaGetLastError();
+    e = batch::enqueue_merge_status(
+        reinterpret_cast<const int*>(static_cast<unsigned char*>(b->d_ws) + total - 256),
+        b->d_status, st);
     if (e != cudaSuccess) return bfail(DPMA_ERR_CUDA, std::string("status merge: ") + cudaGetErrorString(e));
   }
   return DPMA_OK;
 }
 
+// Host-only validation of a descriptor array.
+dpma_status validate(const dpma_volume_desc* descs, int count) {
+  if (count < 0 || (count > 0 && !descs)) return bfail(DPMA_ERR_INVALID_ARG, "bad descriptor array");
+  for (int i = 0; i < count; ++i) {
+    const dpma_volume_desc& d = descs[i];
+    const std::string at = "descriptor " + std::to_string(i) + ": ";
+    if (!d.volume) return bfail(DPMA_ERR_INVALID_ARG, at + "null volume");
+    if (d.out_offset < 0 || d.out_offset % 16 != 0)
+      return bfail(DPMA_ERR_INVALID_ARG, at + "out_offset must be a non-negative multiple of 16");
+    if (dpma_workspace_size(d.L, d.M, d.N, (dpma_dtype)d.dtype, d.K) == 0)
+      return bfail(DPMA_ERR_INVALID_ARG, at + "bad dimensions, dtype or K");
+    if (d.dtype != DPMA_F32) {
+      const double vmax = d.dtype == DPMA_U8 ? 255.0 : 65535.0;
+      if (log2_bound_2d(d.L, d.M, d.N, vmax, d.K) > 125.0 ||
+          log2_bound_3d(d.L, d.M, d.N, vmax, d.K) > 125.0)
+        return bfail(DPMA_ERR_OVERFLOW, at + "moments could exceed the int128 range");
+    }
+  }
+  return DPMA_OK;
+}
+
 }  // namespace
+
+namespace dpma {
+// Shared with the serving loop: host-only descriptor checks.
+dpma_status validate_descs(const dpma_volume_desc* descs, int count) { return validate(descs, count); }
+}  // namespace dpma
 
 extern "C" {
 
@@ -518,71 +649,13 @@ dpma_status dpma_batch_create(const dpma_volume_desc* descs, int count, int flag
   *plan = nullptr;
   if (count < 0 || (count > 0 && !descs)) return bfail(DPMA_ERR_INVALID_ARG, "bad descriptor array");
   if (flags & ~DPMA_BATCH_AUTOTUNE) return bfail(DPMA_ERR_INVALID_ARG, "unknown flags");
-  // host-only validation first
-  for (int i = 0; i < count; ++i) {
-    const dpma_volume_desc& d = descs[i];
-    if (!d.volume) return bfail(DPMA_ERR_INVALID_ARG, "descriptor " + std::to_string(i) + ": null volume");
-    if (d.out_offset < 0 || d.out_offset % 16 != 0)
-      return bfail(DPMA_ERR_INVALID_ARG, "descriptor " + std::to_string(i) + ": out_offset must be a non-negative multiple of 16");
-    const size_t need = dpma_workspace_size(d.L, d.M, d.N, (dpma_dtype)d.dtype, d.K);
-    if (need == 0)
-      return bfail(DPMA_ERR_INVALID_ARG, "descriptor " + std::to_string(i) + ": bad dimensions, dtype or K");
-    if (d.dtype != DPMA_F32) {
-      const double vmax = d.dtype == DPMA_U8 ? 255.0 : 65535.0;
-      if (log2_bound_2d(d.L, d.M, d.N, vmax, d.K) > 125.0 || log2_bound_3d(d.L, d.M, d.N, vmax, d.K) > 125.0)
-        return bfail(DPMA_ERR_OVERFLOW, "descriptor " + std::to_string(i) + ": moments could exceed the int128 range");
-    }
-  }
+  dpma_status vs = validate(descs, count);
+  if (vs != DPMA_OK) return vs;
   dpma_batch* b = new dpma_batch();
-  b->count = count;
   b->descs.assign(descs, descs + count);
   cudaError_t e = cudaGetDevice(&b->device);
   if (e != cudaSuccess) { free_plan(b); return bfail(DPMA_ERR_CUDA, "no current CUDA device"); }
-
-  // classify: fused (integer, L <= 256, images fit shared memory) or single
-  size_t max_words = 0;
-  int64_t t_total = 0;
-  bool k_used[kMaxK + 1] = {};
-  for (int i = 0; i < count; ++i) {
-    const dpma_volume_desc& d = descs[i];
-    const int P = num_images(d.K);
-    bool fused = d.dtype != DPMA_F32 && d.L <= 32 * kMaxXSlots;
-    BTask t{};
-    if (fused) {
-      const double vmax = d.dtype == DPMA_U8 ? 255.0 : 65535.0;
-      const int64_t line = longest_line(d.L, d.M, d.N);
-      t.wide = vmax * (double)line >= 65536.0 ? 1 : 0;
-      int64_t pix = 0;
-      int64_t maxF = 1, maxpix = 0;
-      for (int k = 0; k < P; ++k) {
-        ImageGeom g;
-        image_geom(k, d.L, d.M, d.N, &g);
-        t.img_off[k] = (int)pix;
-        pix += (g.S * g.F + 1) & ~int64_t(1);  // even: 16-bit pixels pair up in words
-        maxF = std::max(maxF, std::max(g.F, g.S));
-        maxpix = std::max(maxpix, g.S * g.F);
-      }
-      const int64_t words = t.wide ? pix : pix / 2;
-      if ((size_t)words * 4 + kPartBytes > (size_t)kSmemLimit || pix > (1ll << 30)) fused = false;
-      if (fused) {
-        t.vol = d.volume;
-        t.L = (int)d.L; t.M = (int)d.M; t.N = (int)d.N;
-        t.dtype = d.dtype; t.K = d.K; t.P = P;
-        t.words = (int)words;
-        // |I f^b| summed over a row stays inside int64?
-        const double bits = std::log2(vmax * (double)line + 1) + d.K * std::log2((double)maxF + 1) +
-                            std::log2((double)maxF + 1);
-        t.r64 = bits < 62.0 ? 1 : 0;
-        t.t_off = t_total;
-        t.out_off = d.out_offset;
-        t_total += (int64_t)P * num_2d(d.K);
-        b->tasks.push_back(t);
-        max_words = std::max(max_words, (size_t)words);
-        k_used[d.K] = true;
-      }
-    }
-    if (!fused) b->single.push_back(i);
-  }
+  batch::classify(descs, count, &b->cls);
 
   auto oom = [&](cudaError_t err, const char* what) {
     free_plan(b);
@@ -591,45 +664,27 @@ dpma_status dpma_batch_create(const dpma_volume_desc* descs, int count, int flag
   };
   e = cudaMalloc(&b->d_status, sizeof(int));
   if (e != cudaSuccess) return oom(e, "batch status");
-  if (!b->tasks.empty()) {
-    // largest volumes first so the queue ends with short tasks
-    std::vector<int> order(b->tasks.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-      const BTask &a = b->tasks[x], &c = b->tasks[y];
-      return (int64_t)a.L * a.M * a.N > (int64_t)c.L * c.M * c.N;
-    });
-    e = cudaMalloc(&b->d_tasks, sizeof(BTask) * b->tasks.size());
+  const std::vector<BTask>& tasks = b->cls.tasks;
+  if (!tasks.empty()) {
+    const std::vector<int> order = batch::lpt_order(tasks);
+    e = cudaMalloc(&b->d_tasks, sizeof(BTask) * tasks.size());
     if (e == cudaSuccess) e = cudaMalloc(&b->d_order, sizeof(int) * order.size());
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_T, sizeof(i128) * (size_t)std::max<int64_t>(1, t_total));
+    if (e == cudaSuccess)
+      e = cudaMalloc(&b->d_T, sizeof(i128) * (size_t)std::max<int64_t>(1, b->cls.t_total));
     if (e != cudaSuccess) return oom(e, "batch buffers");
-    e = cudaMemcpy(b->d_tasks, b->tasks.data(), sizeof(BTask) * b->tasks.size(), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(b->d_tasks, tasks.data(), sizeof(BTask) * tasks.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
       e = cudaMemcpy(b->d_order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = batch::prepare_plans();
     if (e != cudaSuccess) return oom(e, "batch upload");
-    // packed combine plans of every order present
-    std::vector<int64_t> words;
-    for (int K = 0; K <= kMaxK; ++K) {
-      if (!k_used[K]) continue;
-      std::vector<int64_t> w(8192);
-      int off[kMaxK + 1];
-      const size_t n = pack_combine_plan(K, w.data(), w.size(), off);
-      if (n == 0) { free_plan(b); return bfail(DPMA_ERR_INTERNAL, "combine plan unavailable"); }
-      for (int d = 0; d <= kMaxK; ++d) b->plan_off[K][d] = (int)words.size() + off[d];
-      words.insert(words.end(), w.begin(), w.begin() + n);
-    }
-    e = cudaMalloc(&b->d_plans, sizeof(int64_t) * words.size());
-    if (e == cudaSuccess)
-      e = cudaMemcpy(b->d_plans, words.data(), sizeof(int64_t) * words.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return oom(e, "combine plans");
-    b->smem = (size_t)kPartBytes + max_words * 4;
+    b->smem = batch::fused_smem(b->cls.max_words);
     b->threads = 512;
-    b->grid = grid_for(b, 512);
+    b->grid = batch::fused_grid(b->smem, 512, (int)tasks.size());
   }
-  if (!b->single.empty()) {
+  if (!b->cls.single.empty()) {
     size_t ws = 0;
-    for (int i : b->single) {
+    for (int i : b->cls.single) {
       const dpma_volume_desc& d = descs[i];
       ws = std::max(ws, dpma_workspace_size(d.L, d.M, d.N, (dpma_dtype)d.dtype, d.K));
       e = prepare_combine(d.K);  // resident before any stream capture
@@ -640,10 +695,10 @@ dpma_status dpma_batch_create(const dpma_volume_desc* descs, int count, int flag
     b->ws_bytes = ws;
   }
 
-  if ((flags & DPMA_BATCH_AUTOTUNE) && !b->tasks.empty()) {
-    // time both CTA sizes on the real inputs and keep the faster one
+  if ((flags & DPMA_BATCH_AUTOTUNE) && !tasks.empty()) {
+    // time both CTA sizes of the fused launch on the real inputs, keep the faster
     void* scratch = nullptr;
-    size_t ob = 0;
+    size_t ob = 16;
     for (const dpma_volume_desc& d : b->descs)
       ob = std::max(ob, (size_t)d.out_offset + (size_t)num_moments(d.K) * 16);
     e = cudaMalloc(&scratch, ob);
@@ -657,15 +712,12 @@ dpma_status dpma_batch_create(const dpma_volume_desc* descs, int count, int flag
     int best_nt = 512, best_grid = b->grid;
     for (int nt : {256, 512}) {
       b->threads = nt;
-      b->grid = grid_for(b, nt);
-      const std::vector<int> keep = b->single;
-      b->single.clear();  // time the fused launch only
-      enqueue_batch(b, scratch, st);
+      b->grid = batch::fused_grid(b->smem, nt, (int)tasks.size());
+      enqueue_batch(b, scratch, st, false);
       cudaEventRecord(e0, st);
-      for (int r = 0; r < 3; ++r) enqueue_batch(b, scratch, st);
+      for (int r = 0; r < 3; ++r) enqueue_batch(b, scratch, st, false);
       cudaEventRecord(e1, st);
       cudaEventSynchronize(e1);
-      b->single = keep;
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       if (ms < best) { best = ms; best_nt = nt; best_grid = b->grid; }
@@ -703,8 +755,8 @@ dpma_status dpma_batch_status(dpma_batch* plan, void* stream) {
 int dpma_batch_info(const dpma_batch* plan, int what) {
   if (!plan) return -1;
   switch (what) {
-    case 0: return (int)plan->tasks.size();
-    case 1: return (int)plan->single.size();
+    case 0: return (int)plan->cls.tasks.size();
+    case 1: return (int)plan->cls.single.size();
     case 2: return plan->threads;
     case 3: return plan->grid;
     case 4: return (int)plan->smem;

@@ -1,0 +1,56 @@
+// Internal interface of the batched path (batch.cu), shared by the batch plan
+// of the C ABI and the serving loop (server.cu).
+#pragma once
+#include <vector>
+
+#include "../../include/dpma.h"
+#include "dpma_internal.cuh"
+
+namespace dpma {
+namespace batch {
+
+// One volume of a fused launch (device-resident task table entry).
+struct BTask {
+  const void* vol;
+  int L, M, N;
+  int dtype, K, P;
+  int wide;   // 1: 32-bit pixels, 0: 16-bit pixels
+  int r64;    // 1: row power sums fit int64
+  int words;  // 32-bit words of shared memory the images take
+  int img_off[kMaxImages];  // first pixel of each image (even, in pixel units)
+  int64_t t_off;            // first 2-D moment of this volume in T (int128 units)
+  int64_t out_off;          // byte offset of this volume's moments in the output
+};
+
+struct Classified {
+  std::vector<BTask> tasks;       // fused volumes, in descriptor order
+  std::vector<int> fused_index;   // descriptor index of each task
+  std::vector<int> single;        // descriptors for the single-volume path
+  int64_t t_total = 0;            // int128 2-D moments of all tasks
+  size_t max_words = 0;           // largest image footprint in 32-bit words
+};
+
+// Sorts valid descriptors into fused tasks (integer volumes, L <= 256, images
+// within shared memory) and single-volume ones.  Host only.
+void classify(const dpma_volume_desc* d, int n, Classified* c);
+// Processing order of the fused queue: largest volumes first.
+std::vector<int> lpt_order(const std::vector<BTask>& tasks);
+// Dynamic shared memory of a fused launch whose largest task takes max_words.
+size_t fused_smem(size_t max_words);
+// CTAs of a fused launch: resident capacity, at most ntasks.
+int fused_grid(size_t smem, int threads, int ntasks);
+// Packed combine plans of every order 0..8 resident on the current device
+// (built once per device; synchronous the first time).
+cudaError_t prepare_plans();
+// Enqueues the fused projection + 2-D moment launch and the batched combine
+// for n tasks already in device memory; `out` is the base the tasks' out_off
+// refer to; *d_status becomes 7 if an exact division left a remainder.
+// d_counter must be zero when the launch starts (the caller clears it).
+cudaError_t enqueue_fused(const BTask* d_tasks, const int* d_order, int n, int* d_counter,
+                          i128* d_T, size_t smem, int threads, int grid, void* out,
+                          int* d_status, cudaStream_t st);
+// Enqueues *dst = max(*dst, *src) on the device.
+cudaError_t enqueue_merge_status(const int* src, int* dst, cudaStream_t st);
+
+}  // namespace batch
+}  // namespace dpma

@@ -202,3 +202,15 @@ def test_batch_arguments_checked_on_the_host(lib):
     assert lib.dpma_batch_create(arr, 1, 4, ctypes.byref(h)) == 1  # unknown flag
     assert lib.dpma_batch_info(None, 0) == -1
     assert lib.dpma_batch_destroy(None) == 0
+
+
+def test_server_arguments_checked(lib):
+    import paper_2012_08099_gb300 as d
+    h = ctypes.c_void_p()
+    assert lib.dpma_server_create(None, None) == 1
+    bad = d.ServerConfig(-1, 0, 0, 0, 0)
+    assert lib.dpma_server_create(ctypes.byref(bad), ctypes.byref(h)) == 1
+    t = ctypes.c_uint64()
+    assert lib.dpma_server_submit(None, None, ctypes.byref(t)) == 1
+    assert lib.dpma_server_poll(None, 1) == -1
+    assert lib.dpma_server_destroy(None) == 0
