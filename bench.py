@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=400)
     ap.add_argument("--shape", default=None,
                     help="L,M,N of a smaller volume of the same recipe (profiling runs)")
     args = ap.parse_args()
@@ -275,6 +278,12 @@ def run_ours(args):
            "h2d_bytes_per_step": int(vol.nbytes), "d2h_bytes_per_step": int(nm * 8 + 4),
            "ms_per_step": round(e2e_s * 1e3, 4)}
 
+    batched = serving = None
+    if rank == 0 and not args.no_batched:
+        batched = run_batched(dpma, torch)
+    if rank == 0 and not args.no_serving:
+        serving = run_serving(dpma, args.serving_requests)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(vol, args.cpu_budget_s)
@@ -292,10 +301,139 @@ def run_ours(args):
                              + (" (larger: no flush needed)" if vol.nbytes > 129e6 else "")},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": gpu_launches, "clocks": clk,
+            "batched": batched, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------ batched and serving rows
+
+
+def run_batched(dpma, torch, reps=20):
+    """4096 binary ROI masks (u8, sizes log-uniform 8..96, fill 20-80%), K = 4:
+    one graph-captured batched run vs. the same ROIs launched one by one."""
+    from paper_2012_08099_gb300 import synth
+    rb = synth.roi_batch(4096, seed=4)
+    tv = [torch.from_numpy(v).cuda() for v in rb.volumes]
+    n = len(tv)
+    voxels = float(sum(v.size for v in rb.volumes))
+    b = dpma.Batch(tv, [4] * n, [dpma.U8] * n, autotune=True)
+    out = b.out_buffer()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.run(out)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.run(out)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    e1.synchronize()
+    ms_batch = e0.elapsed_time(e1) / reps
+    b.status()
+    # per-volume launches of the single-volume pipeline on one stream
+    lib = dpma.lib()
+    wsb = max(dpma.workspace_size(v.shape[2], v.shape[1], v.shape[0], dpma.U8, 4) for v in rb.volumes)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    out1 = torch.zeros_like(out)
+    sp = ctypes.c_void_p(s.cuda_stream)
+    args = [(ctypes.c_void_p(t.data_ptr()), t.shape[2], t.shape[1], t.shape[0],
+             ctypes.c_void_p(out1.data_ptr() + off)) for t, off in zip(tv, b.offsets)]
+
+    def per_volume():
+        for vp, L_, M_, N_, op in args:
+            rc = lib.dpma_moments_async(vp, L_, M_, N_, dpma.U8, 4, op, sp,
+                                        ctypes.c_void_p(ws.data_ptr()), wsb)
+            if rc:
+                raise dpma.DpmaError(rc, lib.dpma_last_error().decode())
+
+    with torch.cuda.stream(s):
+        per_volume()
+        s.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(s)
+        for _ in range(2):
+            per_volume()
+        f1.record(s)
+    f1.synchronize()
+    ms_single = f0.elapsed_time(f1) / 2
+    return {"workload": "roi_masks_u8_4096_K4", "value": n / (ms_batch * 1e-3),
+            "unit": "volume/s", "voxels_per_s": voxels / (ms_batch * 1e-3),
+            "ms_per_batch": round(ms_batch, 4), "volumes": n, "voxels": int(voxels),
+            "graph_captured": True, "fused_threads": b.info(2), "fused_ctas": b.info(3),
+            "per_volume_launches": {"value": n / (ms_single * 1e-3), "unit": "volume/s",
+                                    "ms_per_batch": round(ms_single, 3)},
+            "speedup_vs_per_volume": round(ms_single / ms_batch, 2),
+            "identical": bool(torch.equal(out, out1))}
+
+
+def run_serving(dpma, n_requests, distinct=48, rate_hz=200.0):
+    """Poisson request stream (mean 200 req/s) of u16 CT-like phantoms, x, y
+    log-uniform 32..512, z 32..300, K uniform in {3,4,6,8}; then the same
+    requests submitted at once (saturation)."""
+    import threading
+    from paper_2012_08099_gb300 import synth
+    reqs = synth.serving_stream(distinct, seed=5, rate_hz=rate_hz)
+    g = np.random.Generator(np.random.PCG64(55))
+    arrivals = np.cumsum(g.exponential(1.0 / rate_hz, size=n_requests))
+    pick = g.integers(0, distinct, size=n_requests)
+    res = {}
+    with dpma.Server(max_inflight=64, streams=4) as srv:
+        for r in reqs[:4]:                       # warm the pinned pools
+            srv.wait(srv.submit(r.volume, r.K))
+        srv.stats(reset=True)
+        tickets = []
+
+        def waiter():
+            for t in iter_tickets():
+                srv.wait(t)
+
+        def iter_tickets():
+            i = 0
+            while i < n_requests:
+                while len(tickets) <= i:
+                    time.sleep(0.0002)
+                yield tickets[i]
+                i += 1
+
+        w = threading.Thread(target=waiter)
+        w.start()
+        t0 = time.perf_counter()
+        for a, j in zip(arrivals, pick):
+            dt = a - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(srv.submit(reqs[j].volume, reqs[j].K))
+        w.join()
+        st = srv.stats(reset=True)
+        vox = float(sum(reqs[j].volume.size for j in pick))
+        res["poisson"] = {"offered_req_per_s": rate_hz, "requests": n_requests,
+                          "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+                          "mean_ms": round(st["mean_ms"], 3), "max_ms": round(st["max_ms"], 3),
+                          "volumes_per_s": round(st["volumes_per_s"], 1),
+                          "voxels_per_s": st["voxels_per_s"], "failed": st["failed"],
+                          "launches": st["launches"]}
+        # saturation: every request at once
+        t0 = time.perf_counter()
+        ts = [srv.submit(reqs[j].volume, reqs[j].K) for j in pick]
+        for t in ts:
+            srv.wait(t)
+        wall = time.perf_counter() - t0
+        st = srv.stats(reset=True)
+        res["saturation"] = {"requests": n_requests, "volumes_per_s": round(n_requests / wall, 1),
+                             "voxels_per_s": vox / wall, "p50_ms": round(st["p50_ms"], 3),
+                             "p99_ms": round(st["p99_ms"], 3), "failed": st["failed"]}
+    res["workload"] = "ct_phantom_u16_poisson_200hz_mixedK"
+    res["distinct_volumes"] = distinct
+    return res
 
 
 # -------------------------------------------------------------- reference
