@@ -179,6 +179,41 @@ dpma_status dpma_image_moments(const void* images, int64_t L, int64_t M, int64_t
 dpma_status dpma_combine(const void* moments2d, dpma_dtype dtype, int K, void* out, void* stream,
                          int* status);
 
+/*
+ * 3-D moments from given projection images (the tomographic use of the
+ * method, Sec. 3.2: a few chosen projections stand in for a reconstructed
+ * volume).  `images` (device) holds the first max(3, K+1) images of the
+ * table above for an L x M x N volume, back to back in that order and
+ * layout: uint32 pixels for DPMA_U8 / DPMA_U16 (any integer line sums),
+ * IEEE doubles for DPMA_F32.  `dtype` only selects the pixel type and the
+ * magnitude bound (the largest voxel value 255 / 65535 bounds the int128
+ * range check).  Runs steps 2 and 3 on `stream` with the library's own
+ * workspace and waits for them.  DPMA_ERR_INTERNAL: an exact integer
+ * division left a remainder, i.e. the integer images are not the
+ * projections of any integer volume.
+ */
+dpma_status dpma_moments_from_projections(const void* images, int64_t L, int64_t M, int64_t N,
+                                          dpma_dtype dtype, int K, void* out, void* stream);
+
+/*
+ * Features derived from the moments (the post-step of Sec. 4), on the
+ * device: `moments` holds dpma_num_moments(K) raw moments as the other entry
+ * points return them (int128 for DPMA_U8 / DPMA_U16, double for DPMA_F32).
+ * `out` (device) receives 3 + 3 * dpma_num_moments(K) doubles:
+ *   out[0..2]              centroid (M100, M010, M001) / M000 in voxel units;
+ *   out[3 .. 3+nm)         central moments mu_pqr (graded order);
+ *   out[3+nm .. 3+2nm)     eta_pqr = mu_pqr / mu_000^((p+q+r)/3 + 1)  (Eq. 17);
+ *   out[3+2nm .. 3+3nm)    mu'_pqr = a^(1+p) b^(1+q) c^(1+r) mu_pqr for the
+ *                          voxel spacings spacing = {a, b, c} (host array;
+ *                          NULL: unit spacing).
+ * The binomial expansion about the centroid runs in double-double arithmetic
+ * from the exact moments; only the results are rounded.  M000 = 0 gives NaN
+ * everywhere; K = 0 gives a NaN centroid (no first-degree moments).  Enqueued on `stream`.  Errors: DPMA_ERR_INVALID_ARG (null
+ * pointer, K or dtype out of range, a non-positive spacing), DPMA_ERR_CUDA.
+ */
+dpma_status dpma_derived_moments(const void* moments, dpma_dtype dtype, int K,
+                                 const double* spacing, double* out, void* stream);
+
 /* ---------------- batches of volumes ---------------- */
 
 /*

@@ -13,6 +13,9 @@ The arithmetic lives in ``oracle.c`` (plain C, compiled on first use into
 * :func:`project` -- Sec. 3.1, Eq. 4 with Eqs. 5-9 and the +-pi/4 families:
   the projection images, pixel by pixel.
 * :func:`image_moments` -- Sec. 1, Eq. 1 on one stored image.
+* :func:`central_moments` -- Sec. 4: centroid and central moments from
+  their definitions over the voxels (with the matching sums of |.| as the
+  error scale).
 
 Volumes are numpy arrays of shape ``(N, M, L)`` (z, y, x) with x fastest,
 i.e. ``V[z, y, x]``.  Moments come in graded order: degree ascending, then
@@ -62,6 +65,8 @@ def _load():
             lib.oracle_image_moments_int.argtypes = [vp, i64, i64, i64, i64, ip, vp]
             lib.oracle_image_moments_f64.argtypes = [vp, i64, i64, i64, i64, ip, vp]
             lib.oracle_image_geometry.argtypes = [ip, i64, i64, i64] + [ctypes.POINTER(i64)] * 4
+            lib.oracle_central_moments.argtypes = [vp, ip, i64, i64, i64, ip, vp, vp, vp]
+            lib.oracle_central_moments.restype = ctypes.c_int
             for f in (
                 lib.oracle_moments_int, lib.oracle_moments_f32, lib.oracle_moments_f32_abs,
                 lib.oracle_project_int, lib.oracle_project_f32, lib.oracle_image_moments_int,
@@ -196,3 +201,24 @@ def image_moments(img: np.ndarray, off_s: int, off_f: int, K: int):
             raise ValueError("bad arguments")
         return out
     raise TypeError(f"unsupported image dtype {img.dtype}")
+
+
+def central_moments(vol: np.ndarray, K: int):
+    """(centroid[3], mu, muabs) of Sec. 4 from the definitions (FP64 numpy arrays).
+
+    ``mu[m] = sum V (x-xbar)^p (y-ybar)^q (z-zbar)^r`` and ``muabs`` the same
+    sum of absolute values, in graded order.
+    """
+    lib = _load()
+    v = np.ascontiguousarray(vol)
+    N, M, L = v.shape
+    eb = {np.dtype(np.uint8): 1, np.dtype(np.uint16): 2, np.dtype(np.float32): 4}[v.dtype]
+    nm = num_moments(K)
+    c = np.empty(3, dtype=np.float64)
+    mu = np.empty(nm, dtype=np.float64)
+    ma = np.empty(nm, dtype=np.float64)
+    rc = lib.oracle_central_moments(v.ctypes.data, eb, L, M, N, K, c.ctypes.data,
+                                    mu.ctypes.data, ma.ctypes.data)
+    if rc:
+        raise ValueError("oracle_central_moments: bad arguments")
+    return c, mu, ma

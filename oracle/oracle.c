@@ -426,3 +426,93 @@ int oracle_image_moments_f64(const double* img, int64_t S, int64_t F, int64_t of
     for (int m = 0; m < nm; ++m) out[m] = acc[m].s + acc[m].c;
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* central moments (Sec. 4): centroid, mu_pqr and the scale |mu|_pqr   */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Straight from the definitions of Sec. 4: the centroid
+ * (M100/M000, M010/M000, M001/M000) from exact sums (int128 for integer
+ * volumes, Neumaier-compensated FP64 for float32), then
+ *     mu_pqr     = sum V (x-xbar)^p (y-ybar)^q (z-zbar)^r
+ *     muabs_pqr  = sum |V| |x-xbar|^p |y-ybar|^q |z-zbar|^r
+ * as compensated FP64 sums over the voxels.  elem_bytes: 1 (uint8),
+ * 2 (uint16) or 4 (float32).  centroid: 3 doubles (NaN when M000 = 0).
+ * Returns 0, or 1 on bad arguments.
+ */
+int oracle_central_moments(const void* vol, int elem_bytes, int64_t L, int64_t M, int64_t N,
+                           int K, double* centroid, double* mu, double* muabs) {
+    if (!vol || !centroid || !mu || !muabs || L < 1 || M < 1 || N < 1 || K < 0 || K > 8) return 1;
+    if (elem_bytes != 1 && elem_bytes != 2 && elem_bytes != 4) return 1;
+    const int nmom = oracle_num_moments(K);
+    int trip[3 * 165];
+    graded_triples(K, trip);
+    double c[3];
+    if (elem_bytes == 4) {
+        const float* f = (const float*)vol;
+        nsum s0 = {0, 0}, sx = {0, 0}, sy = {0, 0}, sz = {0, 0};
+        for (int64_t z = 0; z < N; ++z)
+            for (int64_t y = 0; y < M; ++y)
+                for (int64_t x = 0; x < L; ++x) {
+                    const double v = f[(z * M + y) * L + x];
+                    nsum_add(&s0, v);
+                    nsum_add(&sx, v * (double)x);
+                    nsum_add(&sy, v * (double)y);
+                    nsum_add(&sz, v * (double)z);
+                }
+        const double m0 = s0.s + s0.c;
+        c[0] = (sx.s + sx.c) / m0;
+        c[1] = (sy.s + sy.c) / m0;
+        c[2] = (sz.s + sz.c) / m0;
+    } else {
+        i128 s0 = 0, sx = 0, sy = 0, sz = 0;
+        for (int64_t z = 0; z < N; ++z)
+            for (int64_t y = 0; y < M; ++y)
+                for (int64_t x = 0; x < L; ++x) {
+                    const i128 v = load_int(vol, elem_bytes, (z * M + y) * L + x);
+                    s0 += v;
+                    sx += v * x;
+                    sy += v * y;
+                    sz += v * z;
+                }
+        const long double m0 = (long double)s0;
+        c[0] = (double)((long double)sx / m0);
+        c[1] = (double)((long double)sy / m0);
+        c[2] = (double)((long double)sz / m0);
+    }
+    for (int i = 0; i < 3; ++i) centroid[i] = c[i];
+    nsum* acc = (nsum*)calloc((size_t)nmom, sizeof(nsum));
+    nsum* aab = (nsum*)calloc((size_t)nmom, sizeof(nsum));
+    if (!acc || !aab) { free(acc); free(aab); return 1; }
+    double xp[9], yp[9], zp[9];
+    for (int64_t z = 0; z < N; ++z) {
+        zp[0] = 1.0;
+        for (int e = 1; e <= K; ++e) zp[e] = zp[e - 1] * ((double)z - c[2]);
+        for (int64_t y = 0; y < M; ++y) {
+            yp[0] = 1.0;
+            for (int e = 1; e <= K; ++e) yp[e] = yp[e - 1] * ((double)y - c[1]);
+            for (int64_t x = 0; x < L; ++x) {
+                const int64_t idx = (z * M + y) * L + x;
+                const double v = elem_bytes == 4 ? (double)((const float*)vol)[idx]
+                                                 : (double)load_int(vol, elem_bytes, idx);
+                if (v == 0.0) continue;
+                xp[0] = 1.0;
+                for (int e = 1; e <= K; ++e) xp[e] = xp[e - 1] * ((double)x - c[0]);
+                for (int m = 0; m < nmom; ++m) {
+                    const int* t = trip + 3 * m;
+                    const double w = xp[t[0]] * yp[t[1]] * zp[t[2]];
+                    nsum_add(&acc[m], v * w);
+                    nsum_add(&aab[m], (v < 0 ? -v : v) * (w < 0 ? -w : w));
+                }
+            }
+        }
+    }
+    for (int m = 0; m < nmom; ++m) {
+        mu[m] = acc[m].s + acc[m].c;
+        muabs[m] = aab[m].s + aab[m].c;
+    }
+    free(acc);
+    free(aab);
+    return 0;
+}

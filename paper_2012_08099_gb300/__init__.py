@@ -105,6 +105,9 @@ def lib():
                 "dpma_batch_info": (ip, [vp, ip]),
                 "dpma_batch_destroy": (ip, [vp]),
                 "dpma_moments_batched": (ip, [ctypes.POINTER(VolumeDesc), ip, vp, vp]),
+                "dpma_moments_from_projections": (ip, [vp, i64, i64, i64, ip, ip, vp, vp]),
+                "dpma_derived_moments": (ip, [vp, ip, ip, ctypes.POINTER(ctypes.c_double), vp,
+                                              vp]),
                 "dpma_server_create": (ip, [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]),
                 "dpma_server_submit": (ip, [vp, ctypes.POINTER(VolumeDesc),
                                             ctypes.POINTER(ctypes.c_uint64)]),
@@ -323,6 +326,41 @@ def moments_noalloc(volume, K: int, out, dtype: int | None = None, stream=None):
     _check(lib().dpma_moments_noalloc(ctypes.c_void_p(volume.data_ptr()), L, M, N, dt, K,
                                       ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out
+
+
+def moments_from_projections(images, L: int, M: int, N: int, K: int, dtype: int, stream=None):
+    """3-D moments from projection images already on the device.
+
+    ``images``: a CUDA tensor holding the first max(3, K+1) images back to
+    back (uint32 pixels for integer dtypes, float64 for F32), as
+    :func:`project` lays them out.  Returns exact ints or a float64 numpy array.
+    """
+    import torch
+    nm = num_moments(K)
+    out = torch.empty((nm, 2) if dtype != F32 else (nm,),
+                      dtype=torch.int64 if dtype != F32 else torch.float64, device=images.device)
+    _check(lib().dpma_moments_from_projections(ctypes.c_void_p(images.data_ptr()), L, M, N, dtype,
+                                               K, ctypes.c_void_p(out.data_ptr()),
+                                               _stream_ptr(stream)))
+    h = out.cpu().numpy()
+    return h if dtype == F32 else int128_to_ints(h)
+
+
+def derived_moments(moments, K: int, dtype: int, spacing=None, stream=None) -> dict:
+    """Centroid, mu_pqr, eta_pqr (Eq. 17) and physical-unit mu'_pqr (Sec. 4).
+
+    ``moments``: the CUDA tensor a moment call returned.  Returns numpy arrays.
+    """
+    import torch
+    nm = num_moments(K)
+    out = torch.empty(3 + 3 * nm, dtype=torch.float64, device=moments.device)
+    sp = (ctypes.c_double * 3)(*spacing) if spacing is not None else None
+    _check(lib().dpma_derived_moments(ctypes.c_void_p(moments.data_ptr()), dtype, K, sp,
+                                      ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    torch.cuda.synchronize(moments.device)
+    h = out.cpu().numpy()
+    return {"centroid": h[:3], "mu": h[3:3 + nm], "eta": h[3 + nm:3 + 2 * nm],
+            "mu_phys": h[3 + 2 * nm:]}
 
 
 # ------------------------------------------------------------ profiling

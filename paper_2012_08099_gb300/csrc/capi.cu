@@ -428,6 +428,39 @@ dpma_status dpma_combine(const void* moments2d, dpma_dtype dtype, int K, void* o
   return DPMA_OK;
 }
 
+dpma_status dpma_moments_from_projections(const void* images, int64_t L, int64_t M, int64_t N,
+                                          dpma_dtype dtype, int K, void* out, void* stream) {
+  if (!images || !out) return fail(DPMA_ERR_INVALID_ARG, "null image or output pointer");
+  dpma_status s = check_args(L, M, N, dtype, K);
+  if (s != DPMA_OK) return s;
+  cudaError_t e = prepare_combine(K);
+  if (e != cudaSuccess) return cuda_fail(e, "combine plan");
+  DeviceState* ds = state_for_current_device(nullptr);
+  if (!ds) return fail(DPMA_ERR_CUDA, "no current CUDA device");
+  std::lock_guard<std::mutex> lk(ds->mu);
+  const Layout w = layout(L, M, N, dtype, K);
+  e = ensure_buffer(&ds->ws, &ds->ws_bytes, w.total);
+  if (e != cudaSuccess) return cuda_fail(e, "workspace");
+  unsigned char* ws = static_cast<unsigned char*>(ds->ws);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int* status = reinterpret_cast<int*>(ws + w.off_status);
+  e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "clear status");
+  const bool fl = is_float(dtype);
+  e = launch_image_moments(images, w.set, K, fl, ws + w.off_part, ws + w.off_m2d, st);
+  if (e != cudaSuccess) return cuda_fail(e, "image moment kernel");
+  e = launch_combine(ws + w.off_m2d, K, fl, out, status, st);
+  if (e != cudaSuccess) return cuda_fail(e, "combine kernel");
+  int h = 0;
+  e = cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+  if (h) return fail(DPMA_ERR_INTERNAL,
+                     "the projections are not those of any integer volume (a combine division "
+                     "left a remainder)");
+  return DPMA_OK;
+}
+
 dpma_status dpma_stage_timing(int enable) {
   std::lock_guard<std::mutex> lk(g_timing_mu);
   g_timing = enable != 0;
