@@ -64,9 +64,11 @@ template <typename T, int P> struct TileCfg {
   static constexpr bool FL = std::is_same<T, float>::value;
   static constexpr int BYT = (FL && P >= 6) ? 2 : 4;
   static constexpr int BY = BYT * TY;
-  // resident CTAs per SM: integer state fits 128 registers per thread, so
-  // two CTAs share an SM; float state (hi, lo pairs) needs one CTA
-  static constexpr int MINB = FL ? 1 : 2;
+  // resident CTAs per SM (measured): two for every integer case and for
+  // float volumes with 4 x 2 micro-tiles, where the extra warps hide more
+  // latency than the few spills cost; one for float volumes with 4 or 5
+  // images, whose 4 x 4 micro-tiles would spill heavily at 128 registers
+  static constexpr int MINB = FL ? ((P == 4 || P == 5) ? 1 : 2) : 2;
   // ring depth: about 64 KB of slices in flight per SM, 4 to 16 stages
   static constexpr int SLICE = BY * XT * (int)sizeof(T);
   static constexpr int FLIGHT = 65536 / MINB;
@@ -138,13 +140,17 @@ __device__ __forceinline__ void ts_acc(float& hi, float& lo, float v) {
   hi = t;
 }
 
-// Two independent (hi, lo) += v updates as packed f32x2 operations.
-__device__ __forceinline__ void ts_acc2(float& h0, float& l0, float v0, float& h1, float& l1,
-                                        float v1) {
-  unsigned long long H, Lo, V, t, bb, x, y, e;
-  asm("mov.b64 %0, {%1,%2};" : "=l"(H) : "f"(h0), "f"(h1));
-  asm("mov.b64 %0, {%1,%2};" : "=l"(Lo) : "f"(l0), "f"(l1));
-  asm("mov.b64 %0, {%1,%2};" : "=l"(V) : "f"(v0), "f"(v1));
+// Float pairs held as one 64-bit register (low half first) so that packed
+// f32x2 operations need no register moves.
+__device__ __forceinline__ uint64_t pk(float a, float b) {
+  return (uint64_t)__float_as_uint(a) | ((uint64_t)__float_as_uint(b) << 32);
+}
+__device__ __forceinline__ float half_of(uint64_t p, int h) {
+  return __uint_as_float(h ? (uint32_t)(p >> 32) : (uint32_t)p);
+}
+// (H, Lo) += V for two independent pairs at once (TwoSum, packed).
+__device__ __forceinline__ void ts2(uint64_t& H, uint64_t& Lo, uint64_t V) {
+  uint64_t t, bb, x, y, e;
   asm("add.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(H), "l"(V));
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(bb) : "l"(t), "l"(H));
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(x) : "l"(t), "l"(bb));
@@ -152,8 +158,7 @@ __device__ __forceinline__ void ts_acc2(float& h0, float& l0, float v0, float& h
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(y) : "l"(V), "l"(bb));
   asm("add.rn.f32x2 %0, %1, %2;" : "=l"(e) : "l"(x), "l"(y));
   asm("add.rn.f32x2 %0, %1, %2;" : "=l"(Lo) : "l"(Lo), "l"(e));
-  asm("mov.b64 {%0,%1}, %2;" : "=f"(h0), "=f"(h1) : "l"(t));
-  asm("mov.b64 {%0,%1}, %2;" : "=f"(l0), "=f"(l1) : "l"(Lo));
+  H = t;
 }
 
 // (h, l) += (bh, bl): bh enters with TwoSum, bl is added to l (the pair is
@@ -415,29 +420,62 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
       for (int i = 0; i < STAGES && ub + i < ue; ++i) issue_next(i);
   }
 
-  // register state
+  // register state.  Integer volumes: one uint32 per window pixel.  Float
+  // volumes: (hi, lo) TwoSum pairs packed two pixels per 64-bit register --
+  // adjacent columns for images 0, 5, 6 (their windows never shift in x) and
+  // adjacent rows for images 3, 4 (never shift in y) -- so every packed
+  // update works on registers that stay paired from step to step.
+  constexpr int R2 = R / 2, B2 = (BYT + 1) / 2;
   A a0[BYT][R], w3[BYT][R], w4[BYT][R], w5[BYT][R], w6[BYT][R];
-  float a0c[BYT][R], w3c[BYT][R], w4c[BYT][R], w5c[BYT][R], w6c[BYT][R];
+  uint64_t P0h[BYT][R2], P0l[BYT][R2], P5h[BYT][R2], P5l[BYT][R2], P6h[BYT][R2], P6l[BYT][R2];
+  uint64_t P3h[R][B2], P3l[R][B2], P4h[R][B2], P4l[R][B2];
   auto clear_state = [&]() {
+    if constexpr (FL) {
 #pragma unroll
-    for (int r = 0; r < BYT; ++r)
+      for (int r = 0; r < BYT; ++r)
 #pragma unroll
-      for (int c = 0; c < R; ++c) {
-        a0[r][c] = 0; w3[r][c] = 0; w4[r][c] = 0; w5[r][c] = 0; w6[r][c] = 0;
-        if constexpr (FL) {
-          a0c[r][c] = 0.f; w3c[r][c] = 0.f; w4c[r][c] = 0.f; w5c[r][c] = 0.f; w6c[r][c] = 0.f;
+        for (int c = 0; c < R2; ++c) {
+          P0h[r][c] = P0l[r][c] = P5h[r][c] = P5l[r][c] = P6h[r][c] = P6l[r][c] = 0;
         }
-      }
+#pragma unroll
+      for (int q = 0; q < R; ++q)
+#pragma unroll
+        for (int b = 0; b < B2; ++b) P3h[q][b] = P3l[q][b] = P4h[q][b] = P4l[q][b] = 0;
+    } else {
+#pragma unroll
+      for (int r = 0; r < BYT; ++r)
+#pragma unroll
+        for (int c = 0; c < R; ++c) {
+          a0[r][c] = 0; w3[r][c] = 0; w4[r][c] = 0; w5[r][c] = 0; w6[r][c] = 0;
+        }
+    }
   };
   clear_state();
+  // window pixel (value, compensation) by image, in the scalar index space
+  auto g0 = [&](int r, int c, float& lo) -> A {
+    if constexpr (FL) { lo = half_of(P0l[r][c / 2], c & 1); return half_of(P0h[r][c / 2], c & 1); }
+    else { lo = 0.f; return a0[r][c]; }
+  };
+  auto g3 = [&](int r, int q, float& lo) -> A {
+    if constexpr (FL) { lo = half_of(P3l[q][r / 2], r & 1); return half_of(P3h[q][r / 2], r & 1); }
+    else { lo = 0.f; return w3[r][q]; }
+  };
+  auto g4 = [&](int r, int q, float& lo) -> A {
+    if constexpr (FL) { lo = half_of(P4l[q][r / 2], r & 1); return half_of(P4h[q][r / 2], r & 1); }
+    else { lo = 0.f; return w4[r][q]; }
+  };
+  auto g5 = [&](int q, int c, float& lo) -> A {
+    if constexpr (FL) { lo = half_of(P5l[q][c / 2], c & 1); return half_of(P5h[q][c / 2], c & 1); }
+    else { lo = 0.f; return w5[q][c]; }
+  };
+  auto g6 = [&](int q, int c, float& lo) -> A {
+    if constexpr (FL) { lo = half_of(P6l[q][c / 2], c & 1); return half_of(P6h[q][c / 2], c & 1); }
+    else { lo = 0.f; return w6[q][c]; }
+  };
 
   auto emit = [&](IT* dst, A hi, float lo) {
     if constexpr (FL) emit_ff(dst, hi, lo);
     else emit_u(dst, hi);
-  };
-  auto lo_of = [&](const float (&a)[BYT][R], int r, int c) -> float {
-    if constexpr (FL) return a[r][c];
-    else return 0.f;
   };
 
   // Emit what the registers hold for the current segment (its last step was
@@ -452,7 +490,9 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
 #pragma unroll
       for (int c = 0; c < R; ++c) {
         if (xs + c >= L) continue;
-        emit(img + set.base[0] + y * set.F[0] + xs + c, a0[r][c], lo_of(a0c, r, c));
+        float lo;
+        const A hv = g0(r, c, lo);
+        emit(img + set.base[0] + y * set.F[0] + xs + c, hv, lo);
       }
     }
     if constexpr (H3) {  // logical k = (q - zn) mod R holds pixel x+z = xs + k + zn
@@ -464,7 +504,9 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
         for (int q = 0; q < R; ++q) {
           const int k = (int)(((q - zn) % R + R) % R);
           const int64_t f = xs + k + zn;
-          if (f < set.F[3]) emit(img + set.base[3] + y * set.F[3] + f, w3[r][q], lo_of(w3c, r, q));
+          float lo;
+          const A hv = g3(r, q, lo);
+          if (f < set.F[3]) emit(img + set.base[3] + y * set.F[3] + f, hv, lo);
         }
       }
     }
@@ -477,8 +519,9 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
         for (int q = 0; q < R; ++q) {
           const int k = (int)(((q + zn) % R + R) % R);
           const int64_t f = xs + k - zn + (N - 1);
-          if (f >= 0 && f < set.F[4])
-            emit(img + set.base[4] + y * set.F[4] + f, w4[r][q], lo_of(w4c, r, q));
+          float lo;
+          const A hv = g4(r, q, lo);
+          if (f >= 0 && f < set.F[4]) emit(img + set.base[4] + y * set.F[4] + f, hv, lo);
         }
       }
     }
@@ -490,7 +533,11 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
         if (srow >= set.S[5]) continue;
 #pragma unroll
         for (int c = 0; c < R; ++c)
-          if (xs + c < L) emit(img + set.base[5] + srow * set.F[5] + xs + c, w5[q][c], lo_of(w5c, q, c));
+          if (xs + c < L) {
+            float lo;
+            const A hv = g5(q, c, lo);
+            emit(img + set.base[5] + srow * set.F[5] + xs + c, hv, lo);
+          }
       }
     }
     if constexpr (H6) {  // logical k = (q + zn) mod BYT holds row y-z+N-1 = yt + k - zn + N-1
@@ -501,7 +548,11 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
         if (srow < 0 || srow >= set.S[6]) continue;
 #pragma unroll
         for (int c = 0; c < R; ++c)
-          if (xs + c < L) emit(img + set.base[6] + srow * set.F[6] + xs + c, w6[q][c], lo_of(w6c, q, c));
+          if (xs + c < L) {
+            float lo;
+            const A hv = g6(q, c, lo);
+            emit(img + set.base[6] + srow * set.F[6] + xs + c, hv, lo);
+          }
       }
     }
     clear_state();
@@ -608,34 +659,33 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
       }
 
       // ---- 2. images crossing the slice
+      // float voxels as pairs: vc = adjacent columns of one row (how the
+      // 16-byte loads land), vr = adjacent rows of one column
+      uint64_t vc[BYT][R2], vr[R][B2];
       if constexpr (FL) {
-        // register pairs stay fixed for every z phase: images 0, 5, 6 pair
-        // columns (c, c+1) of one window row, images 3, 4 pair rows (r, r+1)
-        // of one window slot
-#pragma unroll
-        for (int r = 0; r < BYT; r += 2)
-#pragma unroll
-          for (int c = 0; c < R; ++c) {
-            if constexpr (H3) {
-              const int q = (c + j) % R;
-              ts_acc2(w3[r][q], w3c[r][q], v[r][c], w3[r + 1][q], w3c[r + 1][q], v[r + 1][c]);
-            }
-            if constexpr (H4) {
-              const int q = (c - j + R) % R;
-              ts_acc2(w4[r][q], w4c[r][q], v[r][c], w4[r + 1][q], w4c[r + 1][q], v[r + 1][c]);
-            }
-          }
 #pragma unroll
         for (int r = 0; r < BYT; ++r)
 #pragma unroll
-          for (int c = 0; c < R; c += 2) {
-            ts_acc2(a0[r][c], a0c[r][c], v[r][c], a0[r][c + 1], a0c[r][c + 1], v[r][c + 1]);
-            if constexpr (H5)
-              ts_acc2(w5[(r + j) % BYT][c], w5c[(r + j) % BYT][c], v[r][c], w5[(r + j) % BYT][c + 1],
-                      w5c[(r + j) % BYT][c + 1], v[r][c + 1]);
+          for (int cp = 0; cp < R2; ++cp) vc[r][cp] = pk(v[r][2 * cp], v[r][2 * cp + 1]);
+#pragma unroll
+        for (int c = 0; c < R; ++c)
+#pragma unroll
+          for (int rp = 0; rp < B2; ++rp) vr[c][rp] = pk(v[2 * rp][c], v[2 * rp + 1][c]);
+#pragma unroll
+        for (int r = 0; r < BYT; ++r)
+#pragma unroll
+          for (int cp = 0; cp < R2; ++cp) {
+            ts2(P0h[r][cp], P0l[r][cp], vc[r][cp]);
+            if constexpr (H5) ts2(P5h[(r + j) % BYT][cp], P5l[(r + j) % BYT][cp], vc[r][cp]);
             if constexpr (H6)
-              ts_acc2(w6[(r - j + R) % BYT][c], w6c[(r - j + R) % BYT][c], v[r][c],
-                      w6[(r - j + R) % BYT][c + 1], w6c[(r - j + R) % BYT][c + 1], v[r][c + 1]);
+              ts2(P6h[(r - j + R) % BYT][cp], P6l[(r - j + R) % BYT][cp], vc[r][cp]);
+          }
+#pragma unroll
+        for (int c = 0; c < R; ++c)
+#pragma unroll
+          for (int rp = 0; rp < B2; ++rp) {
+            if constexpr (H3) ts2(P3h[(c + j) % R][rp], P3l[(c + j) % R][rp], vr[c][rp]);
+            if constexpr (H4) ts2(P4h[(c - j + R) % R][rp], P4l[(c - j + R) % R][rp], vr[c][rp]);
           }
       } else {
 #pragma unroll
@@ -652,48 +702,57 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
 
       // ---- 3. images in the slice: column sums (2), row sums (1), diagonals (7, 8)
       {
-        A cs[R];
-        float csc[R];
-#pragma unroll
-        for (int c = 0; c < R; ++c) {
-          cs[c] = v[0][c];
-          csc[c] = 0.f;
-        }
-#pragma unroll
-        for (int r = 1; r < BYT; ++r) {
-          if constexpr (FL) {
-#pragma unroll
-            for (int c = 0; c < R; c += 2)
-              ts_acc2(cs[c], csc[c], v[r][c], cs[c + 1], csc[c + 1], v[r][c + 1]);
-          } else {
-#pragma unroll
-            for (int c = 0; c < R; ++c) cs[c] += v[r][c];
-          }
-        }
         A* s2 = slot2 + ((size_t)(sb * TY + ty) * XT + xl) * PW;
-        if constexpr (FL) {
-          *reinterpret_cast<float4*>(s2) = make_float4(cs[0], csc[0], cs[1], csc[1]);
-          *reinterpret_cast<float4*>(s2 + 4) = make_float4(cs[2], csc[2], cs[3], csc[3]);
-        } else {
-          *reinterpret_cast<uint4*>(s2) = make_uint4(cs[0], cs[1], cs[2], cs[3]);
-        }
         A rs[BYT];
         float rsc[BYT];
+        if constexpr (FL) {
+          uint64_t csh[R2], csl[R2];  // column sums, pairs of adjacent columns
 #pragma unroll
-        for (int r = 0; r < BYT; ++r) {
-          rs[r] = v[r][0];
-          rsc[r] = 0.f;
-        }
+          for (int cp = 0; cp < R2; ++cp) {
+            csh[cp] = vc[0][cp];
+            csl[cp] = 0;
+          }
 #pragma unroll
-        for (int c = 1; c < R; ++c) {
-          if constexpr (FL) {
+          for (int r = 1; r < BYT; ++r)
 #pragma unroll
-            for (int r = 0; r < BYT; r += 2)
-              ts_acc2(rs[r], rsc[r], v[r][c], rs[r + 1], rsc[r + 1], v[r + 1][c]);
-          } else {
+            for (int cp = 0; cp < R2; ++cp) ts2(csh[cp], csl[cp], vc[r][cp]);
+          *reinterpret_cast<float4*>(s2) = make_float4(half_of(csh[0], 0), half_of(csl[0], 0),
+                                                       half_of(csh[0], 1), half_of(csl[0], 1));
+          *reinterpret_cast<float4*>(s2 + 4) = make_float4(half_of(csh[1], 0), half_of(csl[1], 0),
+                                                           half_of(csh[1], 1), half_of(csl[1], 1));
+          uint64_t rsh[B2], rsl[B2];  // row sums, pairs of adjacent rows
+#pragma unroll
+          for (int rp = 0; rp < B2; ++rp) {
+            rsh[rp] = vr[0][rp];
+            rsl[rp] = 0;
+          }
+#pragma unroll
+          for (int c = 1; c < R; ++c)
+#pragma unroll
+            for (int rp = 0; rp < B2; ++rp) ts2(rsh[rp], rsl[rp], vr[c][rp]);
+#pragma unroll
+          for (int r = 0; r < BYT; ++r) {
+            rs[r] = half_of(rsh[r / 2], r & 1);
+            rsc[r] = half_of(rsl[r / 2], r & 1);
+          }
+        } else {
+          A cs[R];
+#pragma unroll
+          for (int c = 0; c < R; ++c) cs[c] = v[0][c];
+#pragma unroll
+          for (int r = 1; r < BYT; ++r)
+#pragma unroll
+            for (int c = 0; c < R; ++c) cs[c] += v[r][c];
+          *reinterpret_cast<uint4*>(s2) = make_uint4(cs[0], cs[1], cs[2], cs[3]);
+#pragma unroll
+          for (int r = 0; r < BYT; ++r) {
+            rs[r] = v[r][0];
+            rsc[r] = 0.f;
+          }
+#pragma unroll
+          for (int c = 1; c < R; ++c)
 #pragma unroll
             for (int r = 0; r < BYT; ++r) rs[r] += v[r][c];
-          }
         }
         constexpr int per = 16 / BYT;
         if constexpr (FL) {
@@ -750,41 +809,59 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
 
       // ---- 4. hand the leaving window pixels on
       if constexpr (H3) {  // logical 0 (slot j) moves to the left neighbour
+        if constexpr (FL) {
 #pragma unroll
-        for (int r = 0; r < BYT; ++r) {
-          const A sv = w3[r][j];
-          const A rv = __shfl_down_sync(0xffffffffu, sv, 1, 16);
-          w3[r][j] = (tx == TX - 1) ? (A)0 : rv;
-          float sc = 0.f;
-          if constexpr (FL) {
-            sc = w3c[r][j];
-            const float rc = __shfl_down_sync(0xffffffffu, sc, 1, 16);
-            w3c[r][j] = (tx == TX - 1) ? 0.f : rc;
+          for (int rp = 0; rp < B2; ++rp) {
+            const uint64_t sh = P3h[j][rp], sl = P3l[j][rp];
+            const uint64_t rh = __shfl_down_sync(0xffffffffu, (unsigned long long)sh, 1, 16);
+            const uint64_t rl = __shfl_down_sync(0xffffffffu, (unsigned long long)sl, 1, 16);
+            P3h[j][rp] = (tx == TX - 1) ? 0 : rh;
+            P3l[j][rp] = (tx == TX - 1) ? 0 : rl;
+            if (tx == 0) {  // leaves the tile: complete for this CTA
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                A* d = xc + (size_t)(X::E3 + yl + 2 * rp + h) * PW;
+                d[0] = half_of(sh, h);
+                d[1] = half_of(sl, h);
+              }
+            }
           }
-          if (tx == 0) {  // leaves the tile: complete for this CTA
-            A* d = xc + (size_t)(X::E3 + yl + r) * PW;
-            d[0] = sv;
-            if constexpr (FL) d[1] = sc;
+        } else {
+#pragma unroll
+          for (int r = 0; r < BYT; ++r) {
+            const A sv = w3[r][j];
+            const A rv = __shfl_down_sync(0xffffffffu, sv, 1, 16);
+            w3[r][j] = (tx == TX - 1) ? (A)0 : rv;
+            if (tx == 0) xc[X::E3 + yl + r] = sv;  // leaves the tile: complete for this CTA
           }
         }
       }
       if constexpr (H4) {  // logical R-1 moves to the right neighbour
         const int q = (R - 1 - j + R) % R;
+        if constexpr (FL) {
 #pragma unroll
-        for (int r = 0; r < BYT; ++r) {
-          const A sv = w4[r][q];
-          const A rv = __shfl_up_sync(0xffffffffu, sv, 1, 16);
-          w4[r][q] = (tx == 0) ? (A)0 : rv;
-          float sc = 0.f;
-          if constexpr (FL) {
-            sc = w4c[r][q];
-            const float rc = __shfl_up_sync(0xffffffffu, sc, 1, 16);
-            w4c[r][q] = (tx == 0) ? 0.f : rc;
+          for (int rp = 0; rp < B2; ++rp) {
+            const uint64_t sh = P4h[q][rp], sl = P4l[q][rp];
+            const uint64_t rh = __shfl_up_sync(0xffffffffu, (unsigned long long)sh, 1, 16);
+            const uint64_t rl = __shfl_up_sync(0xffffffffu, (unsigned long long)sl, 1, 16);
+            P4h[q][rp] = (tx == 0) ? 0 : rh;
+            P4l[q][rp] = (tx == 0) ? 0 : rl;
+            if (tx == TX - 1) {
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                A* d = xc + (size_t)(X::E4 + yl + 2 * rp + h) * PW;
+                d[0] = half_of(sh, h);
+                d[1] = half_of(sl, h);
+              }
+            }
           }
-          if (tx == TX - 1) {
-            A* d = xc + (size_t)(X::E4 + yl + r) * PW;
-            d[0] = sv;
-            if constexpr (FL) d[1] = sc;
+        } else {
+#pragma unroll
+          for (int r = 0; r < BYT; ++r) {
+            const A sv = w4[r][q];
+            const A rv = __shfl_up_sync(0xffffffffu, sv, 1, 16);
+            w4[r][q] = (tx == 0) ? (A)0 : rv;
+            if (tx == TX - 1) xc[X::E4 + yl + r] = sv;
           }
         }
       }
@@ -795,15 +872,17 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
         A* d = ty > 0 ? mb5 + ((size_t)(sb * TY + ty - 1) * XT + xl) * PW
                       : xc + (size_t)(X::E5 + xl) * PW;
         if constexpr (FL) {
-          *reinterpret_cast<float4*>(d) = make_float4(w5[q][0], w5c[q][0], w5[q][1], w5c[q][1]);
-          *reinterpret_cast<float4*>(d + 4) = make_float4(w5[q][2], w5c[q][2], w5[q][3], w5c[q][3]);
+          *reinterpret_cast<float4*>(d) = make_float4(half_of(P5h[q][0], 0), half_of(P5l[q][0], 0),
+                                                      half_of(P5h[q][0], 1), half_of(P5l[q][0], 1));
+          *reinterpret_cast<float4*>(d + 4) =
+              make_float4(half_of(P5h[q][1], 0), half_of(P5l[q][1], 0), half_of(P5h[q][1], 1),
+                          half_of(P5l[q][1], 1));
+#pragma unroll
+          for (int cp = 0; cp < R2; ++cp) P5h[q][cp] = P5l[q][cp] = 0;
         } else {
           *reinterpret_cast<uint4*>(d) = make_uint4(w5[q][0], w5[q][1], w5[q][2], w5[q][3]);
-        }
 #pragma unroll
-        for (int c = 0; c < R; ++c) {
-          w5[q][c] = 0;
-          if constexpr (FL) w5c[q][c] = 0.f;
+          for (int c = 0; c < R; ++c) w5[q][c] = 0;
         }
       }
       if constexpr (H6) {
@@ -811,15 +890,17 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
         A* d = ty < TY - 1 ? mb6 + ((size_t)(sb * TY + ty + 1) * XT + xl) * PW
                            : xc + (size_t)(X::E6 + xl) * PW;
         if constexpr (FL) {
-          *reinterpret_cast<float4*>(d) = make_float4(w6[q][0], w6c[q][0], w6[q][1], w6c[q][1]);
-          *reinterpret_cast<float4*>(d + 4) = make_float4(w6[q][2], w6c[q][2], w6[q][3], w6c[q][3]);
+          *reinterpret_cast<float4*>(d) = make_float4(half_of(P6h[q][0], 0), half_of(P6l[q][0], 0),
+                                                      half_of(P6h[q][0], 1), half_of(P6l[q][0], 1));
+          *reinterpret_cast<float4*>(d + 4) =
+              make_float4(half_of(P6h[q][1], 0), half_of(P6l[q][1], 0), half_of(P6h[q][1], 1),
+                          half_of(P6l[q][1], 1));
+#pragma unroll
+          for (int cp = 0; cp < R2; ++cp) P6h[q][cp] = P6l[q][cp] = 0;
         } else {
           *reinterpret_cast<uint4*>(d) = make_uint4(w6[q][0], w6[q][1], w6[q][2], w6[q][3]);
-        }
 #pragma unroll
-        for (int c = 0; c < R; ++c) {
-          w6[q][c] = 0;
-          if constexpr (FL) w6c[q][c] = 0.f;
+          for (int c = 0; c < R; ++c) w6[q][c] = 0;
         }
       }
 
@@ -840,8 +921,10 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
           if constexpr (FL) {
             const float4 e0 = *reinterpret_cast<const float4*>(d);
             const float4 e1 = *reinterpret_cast<const float4*>(d + 4);
-            w5[q][0] = e0.x; w5c[q][0] = e0.y; w5[q][1] = e0.z; w5c[q][1] = e0.w;
-            w5[q][2] = e1.x; w5c[q][2] = e1.y; w5[q][3] = e1.z; w5c[q][3] = e1.w;
+            P5h[q][0] = pk(e0.x, e0.z);
+            P5l[q][0] = pk(e0.y, e0.w);
+            P5h[q][1] = pk(e1.x, e1.z);
+            P5l[q][1] = pk(e1.y, e1.w);
           } else {
             const uint4 e0 = *reinterpret_cast<const uint4*>(d);
             w5[q][0] = e0.x; w5[q][1] = e0.y; w5[q][2] = e0.z; w5[q][3] = e0.w;
@@ -855,8 +938,10 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
           if constexpr (FL) {
             const float4 e0 = *reinterpret_cast<const float4*>(d);
             const float4 e1 = *reinterpret_cast<const float4*>(d + 4);
-            w6[q][0] = e0.x; w6c[q][0] = e0.y; w6[q][1] = e0.z; w6c[q][1] = e0.w;
-            w6[q][2] = e1.x; w6c[q][2] = e1.y; w6[q][3] = e1.z; w6c[q][3] = e1.w;
+            P6h[q][0] = pk(e0.x, e0.z);
+            P6l[q][0] = pk(e0.y, e0.w);
+            P6h[q][1] = pk(e1.x, e1.z);
+            P6l[q][1] = pk(e1.y, e1.w);
           } else {
             const uint4 e0 = *reinterpret_cast<const uint4*>(d);
             w6[q][0] = e0.x; w6[q][1] = e0.y; w6[q][2] = e0.z; w6[q][3] = e0.w;

@@ -99,7 +99,6 @@ class Arena {
       }
     }
   }
-  unsigned char* ptr(size_t off) const { return static_cast<unsigned char*>(base_) + off; }
   unsigned char* base() const { return static_cast<unsigned char*>(base_); }
   size_t size() const { return size_; }
   size_t peak() const { return peak_; }
