@@ -127,13 +127,23 @@ struct CombParams {
   int* status;
 };
 
-__global__ void combine_int_kernel(CombParams p) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per moment: the lanes take the terms j = lane, lane + 32, ... of
+// the degree's combination, their partial sums meet in a warp reduction and
+// lane 0 divides by D (exactly, for integers) and writes the moment.
+__device__ __forceinline__ bool moment_of_warp(const CombParams& p, int& n, int& row) {
+  const int m = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nmom = (p.K + 1) * (p.K + 2) * (p.K + 3) / 6;
-  if (m >= nmom) return;
-  int n = 0;
+  if (m >= nmom) return false;
+  n = 0;
   while ((n + 1) * (n + 2) * (n + 3) / 6 <= m) ++n;
-  const int row = m - n * (n + 1) * (n + 2) / 6;
+  row = m - n * (n + 1) * (n + 2) / 6;
+  return true;
+}
+
+__global__ void combine_int_kernel(CombParams p) {
+  int n, row;
+  if (!moment_of_warp(p, n, row)) return;  // uniform across the warp
+  const int lane = threadIdx.x & 31;
   const int64_t* pl = p.plan + p.off[n];
   const int64_t D = pl[0];
   const int nm = (int)pl[1];
@@ -142,27 +152,33 @@ __global__ void combine_int_kernel(CombParams p) {
   const int64_t* C = aa + nm;
   const i128* T = static_cast<const i128*>(p.m2d);
   I256 acc = {{0, 0, 0, 0}};
-  for (int j = 0; j < nm; ++j) {
+  for (int j = lane; j < nm; j += 32) {
     const int a = (int)aa[j];
-    const int b = n - a;
-    const int pair = (a + b) * (a + b + 1) / 2 + (n - a);
+    const int pair = n * (n + 1) / 2 + (n - a);
     mac256(acc, C[row * nm + j], T[img[j] * p.npairs + pair]);
   }
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    I256 o;
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+      o.w[w] = __shfl_xor_sync(0xffffffffu, (unsigned long long)acc.w[w], m);
+    add256(acc, o);
+  }
+  if (lane != 0) return;
   i128 q = 0;
   if (!div256_exact(acc, D, &q)) {
     if (p.status) atomicMax(p.status, kStatusInternal);
     q = 0;
   }
-  static_cast<i128*>(p.out)[m] = q;
+  const int mi = n * (n + 1) * (n + 2) / 6 + row;
+  static_cast<i128*>(p.out)[mi] = q;
 }
 
 __global__ void combine_f32_kernel(CombParams p) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nmom = (p.K + 1) * (p.K + 2) * (p.K + 3) / 6;
-  if (m >= nmom) return;
-  int n = 0;
-  while ((n + 1) * (n + 2) * (n + 3) / 6 <= m) ++n;
-  const int row = m - n * (n + 1) * (n + 2) / 6;
+  int n, row;
+  if (!moment_of_warp(p, n, row)) return;
+  const int lane = threadIdx.x & 31;
   const int64_t* pl = p.plan + p.off[n];
   const double D = (double)pl[0];
   const int nm = (int)pl[1];
@@ -171,13 +187,15 @@ __global__ void combine_f32_kernel(CombParams p) {
   const int64_t* C = aa + nm;
   const float2* T = static_cast<const float2*>(p.m2d);
   double acc = 0.0;
-  for (int j = 0; j < nm; ++j) {
+  for (int j = lane; j < nm; j += 32) {
     const int a = (int)aa[j];
     const int pair = n * (n + 1) / 2 + (n - a);
     const float2 t = T[img[j] * p.npairs + pair];
     acc += (double)C[row * nm + j] * ((double)t.x + (double)t.y);
   }
-  static_cast<double*>(p.out)[m] = acc / D;
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
+  if (lane == 0) static_cast<double*>(p.out)[n * (n + 1) * (n + 2) / 6 + row] = acc / D;
 }
 
 struct DevPlan {
@@ -254,8 +272,8 @@ cudaError_t launch_combine(const void* m2d, int K, bool is_float, void* out, int
   p.out = out;
   p.status = status;
   const int nmom = num_moments(K);
-  const int threads = 64;
-  const int blocks = (nmom + threads - 1) / threads;
+  const int threads = 128;  // four moments per block, one warp each
+  const int blocks = (nmom * 32 + threads - 1) / threads;
   if (is_float) combine_f32_kernel<<<blocks, threads, 0, st>>>(p);
   else combine_int_kernel<<<blocks, threads, 0, st>>>(p);
   return cudaGetLastError();
@@ -296,8 +314,8 @@ cudaError_t launch_combine_packed(const int64_t* dev_words, const int off[kMaxK 
   p.out = out;
   p.status = status;
   const int nmom = num_moments(K);
-  const int threads = 64;
-  const int blocks = (nmom + threads - 1) / threads;
+  const int threads = 128;  // four moments per block, one warp each
+  const int blocks = (nmom * 32 + threads - 1) / threads;
   if (is_float) combine_f32_kernel<<<blocks, threads, 0, st>>>(p);
   else combine_int_kernel<<<blocks, threads, 0, st>>>(p);
   return cudaGetLastError();
