@@ -314,6 +314,8 @@ typedef struct dpma_server_counters {
   int64_t device_bytes_peak;
   double p50_ms, p99_ms, mean_ms, max_ms;
   double volumes_per_s, voxels_per_s; /* completed / (last done - first submit) */
+  int64_t cache_hits;       /* keyed requests served from resident images */
+  int64_t resident_volumes; /* keyed volumes whose images are resident now */
 } dpma_server_counters;
 
 typedef struct dpma_server dpma_server;
@@ -340,6 +342,20 @@ dpma_status dpma_server_create(const dpma_server_config* cfg, dpma_server** serv
  */
 dpma_status dpma_server_submit(dpma_server* server, const dpma_volume_desc* desc,
                                uint64_t* ticket);
+
+/*
+ * As dpma_server_submit, for a volume named by `key` (0: no key).  The
+ * caller promises that one key always names the same volume (dimensions,
+ * element type and voxels).  A keyed volume that runs through the
+ * single-volume pipeline leaves its projection images resident in the
+ * server's arena; a later request with the same key at an order K no higher
+ * than theirs skips the upload and the projection and only takes the image
+ * moments and the combine (the image set of order K is a prefix of the set
+ * of every larger order, with the same geometry).  Resident images are
+ * evicted, least recently used first, when admission needs the memory.
+ */
+dpma_status dpma_server_submit_keyed(dpma_server* server, const dpma_volume_desc* desc,
+                                     uint64_t key, uint64_t* ticket);
 
 /*
  * Waits up to timeout_ms (< 0: no limit, 0: just check) for a request; on

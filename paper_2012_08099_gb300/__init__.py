@@ -62,7 +62,8 @@ class ServerCounters(ctypes.Structure):
                                               "pending", "inflight", "launches",
                                               "device_bytes_peak")] + \
                [(n, ctypes.c_double) for n in ("p50_ms", "p99_ms", "mean_ms", "max_ms",
-                                               "volumes_per_s", "voxels_per_s")]
+                                               "volumes_per_s", "voxels_per_s")] + \
+               [(n, ctypes.c_int64) for n in ("cache_hits", "resident_volumes")]
 
 
 def lib():
@@ -111,6 +112,8 @@ def lib():
                 "dpma_server_create": (ip, [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]),
                 "dpma_server_submit": (ip, [vp, ctypes.POINTER(VolumeDesc),
                                             ctypes.POINTER(ctypes.c_uint64)]),
+                "dpma_server_submit_keyed": (ip, [vp, ctypes.POINTER(VolumeDesc), ctypes.c_uint64,
+                                                  ctypes.POINTER(ctypes.c_uint64)]),
                 "dpma_server_wait": (ip, [vp, ctypes.c_uint64, i64, vp]),
                 "dpma_server_poll": (ip, [vp, ctypes.c_uint64]),
                 "dpma_server_stats": (ip, [vp, ctypes.POINTER(ServerCounters), ip]),
@@ -482,13 +485,15 @@ class Server:
         self.handle = h
         self._meta = {}
 
-    def submit(self, volume: np.ndarray, K: int, dtype: int | None = None) -> int:
+    def submit(self, volume: np.ndarray, K: int, dtype: int | None = None, key: int = 0) -> int:
+        """Queue one request; ``key`` (non-zero) names the volume so that its
+        projection images can stay resident for later requests at K or lower."""
         vol = np.ascontiguousarray(volume)
         dt = dtype_code(vol) if dtype is None else dtype
         N, M, L = vol.shape
         d = VolumeDesc(vol.ctypes.data, L, M, N, dt, K, 0)
         t = ctypes.c_uint64()
-        _check(lib().dpma_server_submit(self.handle, ctypes.byref(d), ctypes.byref(t)))
+        _check(lib().dpma_server_submit_keyed(self.handle, ctypes.byref(d), key, ctypes.byref(t)))
         self._meta[t.value] = (K, dt)
         return t.value
 

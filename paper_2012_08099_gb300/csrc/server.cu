@@ -11,6 +11,14 @@
 // A host callback at the end of each group only records completion; the
 // scheduler then releases the group's device memory and slots, which admits
 // the next requests.  Waiters block on the request's completion.
+//
+// Requests may name their volume with a key.  The images of a keyed
+// single-volume run stay resident in the arena after it completes; a later
+// request for the same key at an order K no higher than the resident one
+// needs no upload and no projection (the image set of order K is a prefix of
+// every larger order's set, with the same geometry) and runs only the image
+// moments and the combine.  Resident images are evicted, least recently used
+// first, when admission needs their memory.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -150,8 +158,21 @@ class PinnedPool {
 
 enum State { kPending = 0, kInFlight = 1, kDone = 2 };
 
+// Images of a completed keyed single-volume run kept in the arena.
+struct CacheEntry {
+  uint64_t key = 0;
+  int64_t L = 0, M = 0, N = 0;
+  int dtype = 0, K = 0;
+  size_t blk = SIZE_MAX;  // arena block [moments | workspace]; images start the workspace
+  size_t off_img = 0;
+  int refs = 0;           // requests in flight reading the images
+  bool stale = false;     // replaced by a newer entry: free once unused
+  uint64_t last_use = 0;
+};
+
 struct Request {
   uint64_t id = 0;
+  uint64_t key = 0;
   dpma_volume_desc d{};  // d.volume: the pinned host copy
   size_t vbytes = 0, obytes = 0, in_cls = 0, out_cls = 0;
   void* h_in = nullptr;
@@ -159,8 +180,13 @@ struct Request {
   bool fused = false;
   size_t ws_bytes = 0;         // single-volume workspace
   size_t t_bytes = 0;          // fused: this volume's 2-D moments
-  size_t blk = SIZE_MAX;       // arena block: [volume | moments | workspace or 2-D moments]
+  // arena blocks: fused: blk = [volume | moments | 2-D moments]; single:
+  // vblk = [volume], blk = [moments | workspace]; resident hit: blk =
+  // [moments | partials | 2-D moments | status] and src holds the images
+  size_t blk = SIZE_MAX, vblk = SIZE_MAX;
   size_t off_vol = 0, off_out = 0, off_ws = 0;
+  CacheEntry* src = nullptr;
+  size_t part_bytes = 0, m2d_bytes = 0;
   double t_submit = 0, t_done = 0;
   State state = kPending;
   dpma_status status = DPMA_OK;
@@ -201,10 +227,13 @@ struct dpma_server {
   int inflight = 0;
   int groups_inflight = 0;
   bool mem_blocked = false;  // the queue head waits for device memory
+  std::vector<CacheEntry*> cache;  // resident images of keyed volumes
+  uint64_t use_clock = 0;
   uint64_t next_id = 1;
 
   // statistics
   int64_t n_submitted = 0, n_completed = 0, n_failed = 0, n_rejected = 0, n_launches = 0;
+  int64_t n_cache_hits = 0;
   int64_t voxels_done = 0;
   double t_first_submit = -1, t_last_done = -1;
   std::vector<double> lat_ms;
@@ -224,10 +253,42 @@ void CUDART_CB on_group_done(void* arg) {
   s->cv_sched.notify_all();
 }
 
-// Device bytes a request holds while in flight.
-size_t request_bytes(Request* r) {
-  return align256(r->vbytes) + align256(r->obytes) +
-         (r->fused ? align256(r->t_bytes) : align256(r->ws_bytes));
+// Device bytes of a request's main block (see Request::blk) and of its
+// separate volume block (single-volume runs only).
+size_t main_bytes(const Request* r) {
+  if (r->src) return align256(r->obytes) + align256(r->part_bytes) + align256(r->m2d_bytes) + 256;
+  if (r->fused) return align256(r->vbytes) + align256(r->obytes) + align256(r->t_bytes);
+  return align256(r->obytes) + align256(r->ws_bytes);
+}
+size_t volume_bytes(const Request* r) { return (r->fused || r->src) ? 0 : align256(r->vbytes); }
+
+// A resident entry for the request's key that serves its order (lock held).
+CacheEntry* find_entry(dpma_server* s, const Request* r) {
+  if (!r->key || r->fused) return nullptr;
+  for (CacheEntry* e : s->cache)
+    if (!e->stale && e->key == r->key && e->L == r->d.L && e->M == r->d.M && e->N == r->d.N &&
+        e->dtype == r->d.dtype && e->K >= r->d.K)
+      return e;
+  return nullptr;
+}
+
+// Frees the least recently used idle entry; false if none (lock held).
+bool evict_one(dpma_server* s) {
+  int best = -1;
+  for (int i = 0; i < (int)s->cache.size(); ++i)
+    if (s->cache[i]->refs == 0 && (best < 0 || s->cache[i]->last_use < s->cache[best]->last_use))
+      best = i;
+  if (best < 0) return false;
+  s->arena.release(s->cache[best]->blk);
+  delete s->cache[best];
+  s->cache.erase(s->cache.begin() + best);
+  return true;
+}
+
+size_t alloc_evicting(dpma_server* s, size_t bytes) {
+  size_t off = s->arena.alloc(bytes);
+  while (off == SIZE_MAX && evict_one(s)) off = s->arena.alloc(bytes);
+  return off;
 }
 
 // Layout of a control block for groups of up to max_group requests.
@@ -250,6 +311,43 @@ void retire_group(dpma_server* s, Group* g) {
     if (r->status == DPMA_OK && st != 0)
       r->status = st == DPMA_ERR_TIMEOUT ? DPMA_ERR_TIMEOUT : DPMA_ERR_INTERNAL;
     r->state = kDone;
+    const bool was_hit = r->src != nullptr;
+    if (r->vblk != SIZE_MAX) s->arena.release(r->vblk);
+    r->vblk = SIZE_MAX;
+    if (r->src) {  // read resident images: release them
+      r->src->refs--;
+      if (r->src->stale && r->src->refs == 0) {
+        s->arena.release(r->src->blk);
+        s->cache.erase(std::find(s->cache.begin(), s->cache.end(), r->src));
+        delete r->src;
+      }
+      r->src = nullptr;
+    }
+    if (r->key && !r->fused && !was_hit && r->status == DPMA_OK && r->blk != SIZE_MAX) {
+      // keep this run's images resident for later requests with the same key
+      for (CacheEntry* e : s->cache)
+        if (e->key == r->key && !e->stale) e->stale = true;
+      for (size_t i = 0; i < s->cache.size();) {
+        CacheEntry* e = s->cache[i];
+        if (e->stale && e->refs == 0) {
+          s->arena.release(e->blk);
+          delete e;
+          s->cache.erase(s->cache.begin() + i);
+        } else {
+          ++i;
+        }
+      }
+      CacheEntry* e = new CacheEntry();
+      e->key = r->key;
+      e->L = r->d.L; e->M = r->d.M; e->N = r->d.N;
+      e->dtype = r->d.dtype;
+      e->K = r->d.K;
+      e->blk = r->blk;
+      e->off_img = r->off_ws;
+      e->last_use = ++s->use_clock;
+      s->cache.push_back(e);
+      r->blk = SIZE_MAX;
+    }
     if (r->blk != SIZE_MAX) s->arena.release(r->blk);
     r->blk = SIZE_MAX;
     s->pinned.put(r->h_in, r->in_cls);
@@ -288,10 +386,26 @@ bool launch_group(dpma_server* s, Group* g, bool fused) {
   unsigned char* base = s->arena.base();
   cudaError_t e = cudaSuccess;
   for (Request* r : g->reqs) {
+    if (r->src) continue;  // resident images: nothing to upload
     e = cudaMemcpyAsync(base + r->off_vol, r->h_in, r->vbytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) break;
   }
-  if (e == cudaSuccess && fused) {
+  if (e == cudaSuccess && !fused && g->reqs[0]->src) {
+    // steps 2 and 3 on the resident images (the first P images of the order
+    // they were made at, with the same geometry)
+    Request* r = g->reqs[0];
+    const bool fl = r->d.dtype == DPMA_F32;
+    const ImageSet set = make_image_set(r->d.L, r->d.M, r->d.N, r->d.K, fl);
+    unsigned char* part = base + r->off_ws;
+    unsigned char* m2d = part + align256(r->part_bytes);
+    int* status = reinterpret_cast<int*>(m2d + align256(r->m2d_bytes));
+    e = cudaMemsetAsync(status, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+      e = launch_image_moments(base + r->src->off_img, set, r->d.K, fl, part, m2d, st);
+    if (e == cudaSuccess) e = launch_combine(m2d, r->d.K, fl, base + r->off_out, status, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  } else if (e == cudaSuccess && fused) {
     // descriptors of the device copies; moments land at arena offsets and each
     // volume's 2-D moments in its own block (T is the arena seen as int128)
     std::vector<dpma_volume_desc> dd(n);
@@ -382,15 +496,44 @@ void scheduler(dpma_server* s) {
       // admission in arrival order while a slot and device memory are free
       while (!s->pending.empty() && s->inflight + (int)admitted.size() < s->cfg.max_inflight) {
         Request* r = s->pending.front();
-        const size_t off = s->arena.alloc(request_bytes(r));
-        if (off == SIZE_MAX) {
+        CacheEntry* hit = find_entry(s, r);
+        if (hit) {  // size the block for steps 2 and 3 alone; pin the images
+          const bool fl = r->d.dtype == DPMA_F32;
+          const ImageSet set = make_image_set(r->d.L, r->d.M, r->d.N, r->d.K, fl);
+          r->part_bytes = moments2d_partials_bytes(set, r->d.K, fl);
+          r->m2d_bytes = (size_t)set.P * num_2d(r->d.K) * (fl ? 8 : 16);
+          r->src = hit;
+          hit->refs++;
+        }
+        const size_t off = alloc_evicting(s, main_bytes(r));
+        size_t voff = SIZE_MAX;
+        if (off != SIZE_MAX && volume_bytes(r)) {
+          voff = alloc_evicting(s, volume_bytes(r));
+          if (voff == SIZE_MAX) s->arena.release(off);
+        }
+        if (off == SIZE_MAX || (volume_bytes(r) && voff == SIZE_MAX)) {
+          if (hit) {
+            hit->refs--;
+            r->src = nullptr;
+          }
           s->mem_blocked = true;  // wait for a completion to free memory
           break;
         }
         r->blk = off;
-        r->off_vol = off;
-        r->off_out = off + align256(r->vbytes);
-        r->off_ws = r->off_out + align256(r->obytes);  // workspace, or 2-D moments
+        r->vblk = voff;
+        if (r->fused) {  // [volume | moments | 2-D moments]
+          r->off_vol = off;
+          r->off_out = off + align256(r->vbytes);
+          r->off_ws = r->off_out + align256(r->obytes);
+        } else {  // [moments | workspace] (+ the volume block), or [moments | step 2-3 scratch]
+          r->off_vol = voff;
+          r->off_out = off;
+          r->off_ws = off + align256(r->obytes);
+        }
+        if (hit) {
+          hit->last_use = ++s->use_clock;
+          s->n_cache_hits++;
+        }
         r->state = kInFlight;
         s->pending.pop_front();
         admitted.push_back(r);
@@ -500,6 +643,11 @@ dpma_status dpma_server_create(const dpma_server_config* cfg, dpma_server** out)
 }
 
 dpma_status dpma_server_submit(dpma_server* s, const dpma_volume_desc* desc, uint64_t* ticket) {
+  return dpma_server_submit_keyed(s, desc, 0, ticket);
+}
+
+dpma_status dpma_server_submit_keyed(dpma_server* s, const dpma_volume_desc* desc, uint64_t key,
+                                     uint64_t* ticket) {
   if (!s || !desc || !ticket) return sfail(DPMA_ERR_INVALID_ARG, "null argument");
   dpma_volume_desc d = *desc;
   d.out_offset = 0;
@@ -514,7 +662,8 @@ dpma_status dpma_server_submit(dpma_server* s, const dpma_volume_desc* desc, uin
   r->fused = !c.tasks.empty();
   if (r->fused) r->t_bytes = (size_t)c.t_total * sizeof(i128);
   else r->ws_bytes = dpma_workspace_size(d.L, d.M, d.N, (dpma_dtype)d.dtype, d.K);
-  if (request_bytes(r) > s->arena.size()) {
+  r->key = key;
+  if (main_bytes(r) + volume_bytes(r) > s->arena.size()) {
     delete r;
     std::lock_guard<std::mutex> lk(s->mu);
     s->n_rejected++;
@@ -590,6 +739,8 @@ dpma_status dpma_server_stats(dpma_server* s, dpma_server_counters* out, int res
   r.pending = (int64_t)s->pending.size();
   r.inflight = s->inflight;
   r.launches = s->n_launches;
+  r.cache_hits = s->n_cache_hits;
+  r.resident_volumes = (int64_t)s->cache.size();
   r.device_bytes_peak = (int64_t)s->arena.peak();
   std::vector<double> v = s->lat_ms;
   if (!v.empty()) {
@@ -613,6 +764,7 @@ dpma_status dpma_server_stats(dpma_server* s, dpma_server_counters* out, int res
   *out = r;
   if (reset) {
     s->n_submitted = s->n_completed = s->n_failed = s->n_rejected = s->n_launches = 0;
+    s->n_cache_hits = 0;
     s->voxels_done = 0;
     s->lat_ms.clear();
     s->t_first_submit = s->t_last_done = -1;
@@ -637,6 +789,7 @@ dpma_status dpma_server_destroy(dpma_server* s) {
     s->pinned.put(kv.second->h_out, kv.second->out_cls);
     delete kv.second;
   }
+  for (CacheEntry* e : s->cache) delete e;  // their memory goes with the arena
   cudaFree(s->ctrl_dev);
   cudaFreeHost(s->ctrl_host);
   delete s;

@@ -134,3 +134,45 @@ def test_wait_with_zero_timeout_polls(dpma):
             except dpma.DpmaError as e:
                 assert e.status == 5  # not finished yet
         assert res == oracle.moments(v, 4)
+
+
+def test_resident_projections_serve_lower_orders(dpma):
+    """A keyed volume's images stay resident: requests for the same key at the
+    same or a lower order skip the upload and the projection, and their
+    results equal a fresh computation."""
+    vol = synth.uniform_volume((40, 200, 300), np.uint16, seed=81)   # single-volume path
+    t = torch.from_numpy(vol.view(np.int16)).cuda()
+    with dpma.Server() as srv:
+        first = srv.wait(srv.submit(vol, 8, key=42))
+        assert first == dpma.moments_values(t, 8, dpma.U16)
+        for K in (6, 4, 8, 0):
+            got = srv.wait(srv.submit(vol, K, key=42))
+            assert got == dpma.moments_values(t, K, dpma.U16), K
+        st = srv.stats()
+        assert st["cache_hits"] == 4 and st["resident_volumes"] == 1
+        # a higher order than the resident one recomputes and replaces it
+        srv2 = None
+    with dpma.Server() as srv:
+        srv.wait(srv.submit(vol, 3, key=5))
+        got = srv.wait(srv.submit(vol, 6, key=5))
+        assert got == dpma.moments_values(t, 6, dpma.U16)
+        got = srv.wait(srv.submit(vol, 5, key=5))
+        assert got == dpma.moments_values(t, 5, dpma.U16)
+        st = srv.stats()
+        assert st["cache_hits"] == 1 and st["resident_volumes"] == 1
+
+
+def test_resident_images_are_evicted_under_pressure(dpma):
+    vols = [synth.uniform_volume((30, 150, 260), np.uint16, seed=90 + i) for i in range(5)]
+    ws = dpma.workspace_size(260, 150, 30, dpma.U16, 6)
+    # room for one request in flight plus about two resident image sets
+    arena = vols[0].nbytes + ws + 8192 + int(2.5 * ws)
+    with dpma.Server(device_bytes=arena) as srv:
+        for i, v in enumerate(vols):
+            srv.wait(srv.submit(v, 6, key=100 + i))
+        st = srv.stats()
+        assert 1 <= st["resident_volumes"] < len(vols)  # older ones were evicted
+        assert st["device_bytes_peak"] <= arena
+        for i, v in enumerate(vols):                     # hits or recomputations: all exact
+            t = torch.from_numpy(v.view(np.int16)).cuda()
+            assert srv.wait(srv.submit(v, 4, key=100 + i)) == dpma.moments_values(t, 4, dpma.U16)
