@@ -140,25 +140,23 @@ __device__ __forceinline__ void ts_acc(float& hi, float& lo, float v) {
   hi = t;
 }
 
-// Float pairs held as one 64-bit register (low half first) so that packed
-// f32x2 operations need no register moves.
+// Float pairs held as one 64-bit register (low half first).
 __device__ __forceinline__ uint64_t pk(float a, float b) {
   return (uint64_t)__float_as_uint(a) | ((uint64_t)__float_as_uint(b) << 32);
 }
 __device__ __forceinline__ float half_of(uint64_t p, int h) {
   return __uint_as_float(h ? (uint32_t)(p >> 32) : (uint32_t)p);
 }
-// (H, Lo) += V for two independent pairs at once (TwoSum, packed).
+// (H, Lo) += V for the two pixels of a pair: two scalar TwoSums.  Scalar
+// float adds issue to both halves of the FMA pipe, while packed f32x2 adds
+// occupy only its heavy half; measured on sm_103a the scalar form is faster
+// although it issues more instructions.
 __device__ __forceinline__ void ts2(uint64_t& H, uint64_t& Lo, uint64_t V) {
-  uint64_t t, bb, x, y, e;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(H), "l"(V));
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(bb) : "l"(t), "l"(H));
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(x) : "l"(t), "l"(bb));
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(x) : "l"(H), "l"(x));
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(y) : "l"(V), "l"(bb));
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(e) : "l"(x), "l"(y));
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(Lo) : "l"(Lo), "l"(e));
-  H = t;
+  float h0 = half_of(H, 0), h1 = half_of(H, 1), l0 = half_of(Lo, 0), l1 = half_of(Lo, 1);
+  ts_acc(h0, l0, half_of(V, 0));
+  ts_acc(h1, l1, half_of(V, 1));
+  H = pk(h0, h1);
+  Lo = pk(l0, l1);
 }
 
 // (h, l) += (bh, bl): bh enters with TwoSum, bl is added to l (the pair is
