@@ -29,27 +29,49 @@ struct RedParams {
   void* m2d;
 };
 
-__global__ void reduce_int_kernel(RedParams p) {
-  const int k = blockIdx.x;
-  const int t = threadIdx.x;
-  if (t >= p.npairs) return;
+// One CTA per (image k, pair t): the threads stride over the image's block
+// partials (all loads independent), then a shared-memory tree adds the
+// thread sums.  Integer sums are exact in int128; float pairs meet in
+// float-float additions.
+constexpr int kRedThreads = 256;
+
+__global__ void __launch_bounds__(kRedThreads) reduce_int_kernel(RedParams p) {
+  const int k = blockIdx.x / p.npairs, t = blockIdx.x % p.npairs;
   const i128* part = static_cast<const i128*>(p.partials);
   i128 acc = 0;
-  for (int64_t b = p.blk_base[k]; b < p.blk_base[k + 1]; ++b) acc += part[b * p.npairs + t];
-  static_cast<i128*>(p.m2d)[k * p.npairs + t] = acc;
+  for (int64_t b = p.blk_base[k] + threadIdx.x; b < p.blk_base[k + 1]; b += kRedThreads)
+    acc += part[b * p.npairs + t];
+  __shared__ i128 sh[kRedThreads];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = kRedThreads / 2; w >= 1; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) static_cast<i128*>(p.m2d)[k * p.npairs + t] = sh[0];
 }
 
-__global__ void reduce_f32_kernel(RedParams p) {
-  const int k = blockIdx.x;
-  const int t = threadIdx.x;
-  if (t >= p.npairs) return;
+__global__ void __launch_bounds__(kRedThreads) reduce_f32_kernel(RedParams p) {
+  const int k = blockIdx.x / p.npairs, t = blockIdx.x % p.npairs;
   const float2* part = static_cast<const float2*>(p.partials);
   float h = 0.f, l = 0.f;
-  for (int64_t b = p.blk_base[k]; b < p.blk_base[k + 1]; ++b) {
-    float2 v = part[b * p.npairs + t];
+  for (int64_t b = p.blk_base[k] + threadIdx.x; b < p.blk_base[k + 1]; b += kRedThreads) {
+    const float2 v = part[b * p.npairs + t];
     ff_add(h, l, v.x, v.y);
   }
-  static_cast<float2*>(p.m2d)[k * p.npairs + t] = make_float2(h, l);
+  __shared__ float2 sh[kRedThreads];
+  sh[threadIdx.x] = make_float2(h, l);
+  __syncthreads();
+  for (int w = kRedThreads / 2; w >= 1; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      float2 a = sh[threadIdx.x];
+      const float2 c = sh[threadIdx.x + w];
+      ff_add(a.x, a.y, c.x, c.y);
+      sh[threadIdx.x] = a;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) static_cast<float2*>(p.m2d)[k * p.npairs + t] = sh[0];
 }
 
 // ---------------- 256-bit helpers ----------------
@@ -246,8 +268,8 @@ cudaError_t launch_reduce_partials(const void* partials, const int64_t* blk_base
   for (int k = 0; k <= P; ++k) p.blk_base[k] = blk_base[k];
   p.P = P;
   p.npairs = num_2d(K);
-  if (is_float) reduce_f32_kernel<<<P, 64, 0, st>>>(p);
-  else reduce_int_kernel<<<P, 64, 0, st>>>(p);
+  if (is_float) reduce_f32_kernel<<<P * p.npairs, kRedThreads, 0, st>>>(p);
+  else reduce_int_kernel<<<P * p.npairs, kRedThreads, 0, st>>>(p);
   return cudaGetLastError();
 }
 
