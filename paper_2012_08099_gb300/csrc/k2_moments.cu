@@ -45,6 +45,7 @@ __device__ __forceinline__ i128 shfl_xor_i128(i128 v, int m) {
   return (i128)(((u128)hi << 64) | lo);
 }
 
+template <int K>
 __global__ void __launch_bounds__(kThreads) k2_int_kernel(K2Params p) {
   const int blk = blockIdx.x;
   int k = 0;
@@ -53,7 +54,6 @@ __global__ void __launch_bounds__(kThreads) k2_int_kernel(K2Params p) {
   const int64_t S = p.set.S[k], F = p.set.F[k];
   const int64_t off_s = p.set.off_s[k], off_f = p.set.off_f[k];
   const uint32_t* img = static_cast<const uint32_t*>(p.images) + p.set.base[k];
-  const int K = p.K;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   // pairs owned by this lane: index lane and lane + 32
@@ -73,9 +73,9 @@ __global__ void __launch_bounds__(kThreads) k2_int_kernel(K2Params p) {
   const int64_t r0 = chunk * kRowsPerBlock;
   const int64_t r1 = (r0 + kRowsPerBlock < S) ? r0 + kRowsPerBlock : S;
   for (int64_t s = r0 + warp; s < r1; s += kWarps) {
-    i128 Fb[kMaxK + 1];
+    i128 Fb[K + 1];
 #pragma unroll
-    for (int b = 0; b <= kMaxK; ++b) Fb[b] = 0;
+    for (int b = 0; b <= K; ++b) Fb[b] = 0;
     const uint32_t* row = img + s * F;
     for (int64_t f0 = lane; f0 < F; f0 += 4 * 32) {
       uint32_t vv[4];
@@ -90,16 +90,14 @@ __global__ void __launch_bounds__(kThreads) k2_int_kernel(K2Params p) {
         const int64_t c = f0 + q * 32 - off_f;
         i128 t = (i128)vv[q];
 #pragma unroll
-        for (int b = 0; b <= kMaxK; ++b) {
-          if (b > K) break;
+        for (int b = 0; b <= K; ++b) {
           Fb[b] += t;
-          t *= (i128)c;
+          if (b < K) t *= (i128)c;
         }
       }
     }
 #pragma unroll
-    for (int b = 0; b <= kMaxK; ++b) {
-      if (b > K) break;
+    for (int b = 0; b <= K; ++b) {
 #pragma unroll
       for (int m = 16; m >= 1; m >>= 1) Fb[b] += shfl_xor_i128(Fb[b], m);
     }
@@ -111,7 +109,7 @@ __global__ void __launch_bounds__(kThreads) k2_int_kernel(K2Params p) {
       for (int e = 0; e < pa[t]; ++e) w *= cs;
       i128 fb = 0;
 #pragma unroll
-      for (int b = 0; b <= kMaxK; ++b)
+      for (int b = 0; b <= K; ++b)
         if (b == pb[t]) fb = Fb[b];
       T[t] += w * fb;
     }
@@ -172,6 +170,7 @@ __device__ __forceinline__ void ff_mul_f(float hi, float lo, float c, float& rh,
   rl = __fsub_rn(e, __fsub_rn(rh, p));
 }
 
+template <int K>
 __global__ void __launch_bounds__(kThreads) k2_f32_kernel(K2Params p) {
   const int blk = blockIdx.x;
   int k = 0;
@@ -180,7 +179,6 @@ __global__ void __launch_bounds__(kThreads) k2_f32_kernel(K2Params p) {
   const int64_t S = p.set.S[k], F = p.set.F[k];
   const int64_t off_s = p.set.off_s[k], off_f = p.set.off_f[k];
   const unsigned long long* plane = static_cast<const unsigned long long*>(p.images) + p.set.base[k];
-  const int K = p.K;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   int pa[2], pb[2];
@@ -199,9 +197,9 @@ __global__ void __launch_bounds__(kThreads) k2_f32_kernel(K2Params p) {
   const int64_t r0 = chunk * kRowsPerBlock;
   const int64_t r1 = (r0 + kRowsPerBlock < S) ? r0 + kRowsPerBlock : S;
   for (int64_t s = r0 + warp; s < r1; s += kWarps) {
-    float Fh[kMaxK + 1], Fl[kMaxK + 1];
+    float Fh[K + 1], Fl[K + 1];
 #pragma unroll
-    for (int b = 0; b <= kMaxK; ++b) { Fh[b] = 0.f; Fl[b] = 0.f; }
+    for (int b = 0; b <= K; ++b) { Fh[b] = 0.f; Fl[b] = 0.f; }
     const unsigned long long* row = plane + s * F;
     for (int64_t f0 = lane; f0 < F; f0 += 4 * 32) {
       unsigned long long raw[4];
@@ -217,16 +215,14 @@ __global__ void __launch_bounds__(kThreads) k2_f32_kernel(K2Params p) {
         if (th == 0.f && tl == 0.f) continue;
         const float c = (float)(f0 + q * 32 - off_f);
 #pragma unroll
-        for (int b = 0; b <= kMaxK; ++b) {
-          if (b > K) break;
+        for (int b = 0; b <= K; ++b) {
           ff_add(Fh[b], Fl[b], th, tl);
-          ff_mul_f(th, tl, c, th, tl);
+          if (b < K) ff_mul_f(th, tl, c, th, tl);
         }
       }
     }
 #pragma unroll
-    for (int b = 0; b <= kMaxK; ++b) {
-      if (b > K) break;
+    for (int b = 0; b <= K; ++b) {
 #pragma unroll
       for (int m = 16; m >= 1; m >>= 1) {
         float oh = __shfl_xor_sync(0xffffffffu, Fh[b], m);
@@ -240,7 +236,7 @@ __global__ void __launch_bounds__(kThreads) k2_f32_kernel(K2Params p) {
       if (pa[t] < 0) continue;
       float fh = 0.f, fl = 0.f;
 #pragma unroll
-      for (int b = 0; b <= kMaxK; ++b)
+      for (int b = 0; b <= K; ++b)
         if (b == pb[t]) { fh = Fh[b]; fl = Fl[b]; }
       for (int e = 0; e < pa[t]; ++e) ff_mul_f(fh, fl, cs, fh, fl);
       ff_add(Th[t], Tl[t], fh, fl);
@@ -291,8 +287,17 @@ cudaError_t launch_image_moments(const void* images, const ImageSet& set, int K,
   p.npairs = num_2d(K);
   const int64_t nblk = blocks_of(set, p.blk_base);
   p.partials = partials;
-  if (is_float) k2_f32_kernel<<<(unsigned)nblk, kThreads, 0, st>>>(p);
-  else k2_int_kernel<<<(unsigned)nblk, kThreads, 0, st>>>(p);
+  switch (K) {
+#define DPMA_K2_CASE(k)                                                   \
+  case k:                                                                 \
+    if (is_float) k2_f32_kernel<k><<<(unsigned)nblk, kThreads, 0, st>>>(p); \
+    else k2_int_kernel<k><<<(unsigned)nblk, kThreads, 0, st>>>(p);          \
+    break;
+    DPMA_K2_CASE(0) DPMA_K2_CASE(1) DPMA_K2_CASE(2) DPMA_K2_CASE(3) DPMA_K2_CASE(4)
+    DPMA_K2_CASE(5) DPMA_K2_CASE(6) DPMA_K2_CASE(7) DPMA_K2_CASE(8)
+#undef DPMA_K2_CASE
+    default: return cudaErrorInvalidValue;
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_reduce_partials(partials, p.blk_base, set.P, K, is_float, m2d, st);
