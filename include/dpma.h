@@ -240,8 +240,8 @@ typedef struct dpma_batch dpma_batch;
  * Plans the moments of `count` volumes (the method of Sec. 3 applied to each
  * volume): validates every descriptor on the host, uploads the task table
  * and allocates the plan's device buffers (synchronous).  Volumes whose
- * images fit on chip (integer element types, L <= 256, images within
- * shared memory) run in one persistent fused launch: projection and 2-D
+ * images fit on chip (integer element types, a z-slice of at most 24 KB,
+ * images within shared memory) run in one persistent fused launch: projection and 2-D
  * moments per volume in shared memory, then one batched combine launch.
  * The others (float32 or larger volumes) run through the single-volume
  * pipeline, one after another on the same stream.  With

@@ -10,15 +10,16 @@
 // memory and reduces them to 2-D moments there; only the 2-D moments reach
 // global memory.  One more launch combines them for every volume.
 //
-// Inside a CTA each warp owns image rows y (y = warp, warp + NW, ...) of every
-// z-slice, so the images whose pixels stay within one row (0, 1, 3, 4) are
-// updated with plain shared-memory read-modify-writes ordered by __syncwarp;
-// the others (2, 5, 6, 7, 8) use shared-memory atomic adds.  Pixels are 16-bit
-// when the longest line times the largest voxel value stays below 2^16 (two
-// pixels per 32-bit word; an atomic add of v << 16 never carries into the
-// neighbour because the sum is bounded), 32-bit otherwise.
+// Inside a CTA a slice is cut into chunks of four consecutive voxels of one
+// row; each thread loads its chunk as one word and adds it to every image with
+// shared-memory atomic adds (two or three 32-bit words per image).  Pixels
+// are 16-bit when the longest line times the largest voxel value stays below
+// 2^16 (two pixels per 32-bit word; a packed add never carries into the
+// neighbour because every sum is bounded), 32-bit otherwise.  The 2-D moments
+// are then taken per image from row power sums of row segments, one thread
+// per segment, folded into T_ab by one warp per image and power b.
 //
-// Volumes the fused kernel does not take (float32, rows wider than 256, or
+// Volumes the fused kernel does not take (float32, slices over 24 KB, or
 // images larger than the shared-memory budget) run through the single-volume
 // pipeline on the same stream, one after another.
 #include <algorithm>
@@ -43,10 +44,11 @@ using dpma::batch::BTask;
 
 namespace {
 
-constexpr int kMaxXSlots = 8;            // fused path: L <= 256 (8 x-values per lane)
-constexpr int kMaxWarps = 16;            // up to 512 threads per CTA
-constexpr int kPartBytes = kMaxWarps * kMax2D * 16;  // per-warp 2-D moment partials
-constexpr int kSmemLimit = 227 * 1024;
+// the 2-D moments T_ab of every image of the volume being reduced (int128)
+constexpr int kPartBytes = kMaxImages * kMax2D * 16;
+constexpr int kSlabWords = 6144;
+constexpr int kSlackWords = 4;  // past the last image: zero adds of a ragged chunk  // one z-slice of a fused volume (24 KB), double-buffered
+constexpr int kSmemLimit = 227 * 1024 - 512;  // dynamic bytes: the rest is static (meta, task id)
 constexpr int kStatusInternal = 7;
 
 
@@ -82,176 +84,325 @@ __device__ __forceinline__ uint32_t pix_get(const uint32_t* sm, int idx) {
 
 // ---------------------------------------------------------------- step 1
 
+// Adds the four consecutive pixels b .. b+3 of one image row, given as the
+// packed pairs p01 = v0 | v1 << 16 and p23 = v2 | v3 << 16 (every v < 2^16).
+// With 16-bit pixels the pairs are shifted onto the pixel words (three words
+// from word b/2) and added with one shared atomic per word; a halfword's sum
+// is bounded below 2^16, so no carry crosses into its neighbour.  The adds
+// are unconditional: a word past the row (a ragged chunk) gets zero, and the
+// image area ends with kSlackWords spare words for the last image.
+template <bool WIDE>
+__device__ __forceinline__ void add4(uint32_t* sm, int b, uint32_t p01, uint32_t p23) {
+  if constexpr (WIDE) {
+    atomicAdd(sm + b, p01 & 0xffffu);
+    atomicAdd(sm + b + 1, p01 >> 16);
+    atomicAdd(sm + b + 2, p23 & 0xffffu);
+    atomicAdd(sm + b + 3, p23 >> 16);
+  } else {
+    const int w = b >> 1;
+    const uint32_t sh = (uint32_t)(b & 1) << 4;
+    atomicAdd(sm + w, p01 << sh);
+    atomicAdd(sm + w + 1, __funnelshift_l(p01, p23, sh));
+    atomicAdd(sm + w + 2, __funnelshift_l(p23, 0u, sh));
+  }
+}
+
+// Slices per projection stage: as many as fit in one buffer with the 16-byte
+// alignment head and the two words a chunk load may read past the stage.
+__host__ __device__ __forceinline__ int stage_slices(int64_t slice_bytes, int N) {
+  const int64_t g = ((int64_t)(kSlabWords - 8) * 4 - 30) / slice_bytes;
+  return (int)(g < 1 ? 1 : (g < N ? g : N));
+}
+
 // Every image of one volume into shared memory (Eq. 4 for the image table of
-// dpma.h): warp w handles rows y = w, w + NW, ... of each z-slice, lane l the
-// columns x = l + 32k.
-template <typename T, bool WIDE, int NT>
-__device__ void project_volume(const BTask& t, uint32_t* sm) {
-  constexpr int NW = NT / 32;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const T* __restrict__ vol = static_cast<const T*>(t.vol);
+// dpma.h).  The volume streams through two shared buffers in stages of G
+// whole z-slices (as many as fit in one buffer): the 16-byte aligned blocks
+// covering the next stage are copied with cp.async while the current stage
+// is processed (a 16-byte block holding a byte of the volume lies in the same
+// mapped page).  A position is a chunk of four consecutive voxels of one row,
+// (y, c) with x0 = 4c; the stage's slices are split into Zg blocks so that
+// positions x blocks fill the CTA, and a thread walks its position through
+// the z of its block.  Four consecutive voxels of a row land on four
+// consecutive pixels of every image but image 1 (z, y), which takes the
+// chunk's sum; image 0 (y, x) does not move with z and is summed in
+// registers over the block.  Every shared update is an atomic add; image k's
+// pixel index moves by a constant per z-step.
+template <typename T, bool WIDE, bool MANY, int NT>
+__device__ __forceinline__ void project_volume(const BTask& t, uint32_t* sm, uint32_t* slab) {
   const int L = t.L, M = t.M, N = t.N, P = t.P;
   const int F3 = L + N - 1, F7 = L + M - 1;
-  const int nxs = (L + 31) >> 5;
   const int* o = t.img_off;
-  for (int z = 0; z < N; ++z) {
-    uint32_t col[kMaxXSlots];
-#pragma unroll
-    for (int k = 0; k < kMaxXSlots; ++k) col[k] = 0;
-    for (int y = warp; y < M; y += NW) {
-      const T* row = vol + ((size_t)z * M + y) * L;
-      uint32_t rsum = 0;
-#pragma unroll
-      for (int k = 0; k < kMaxXSlots; ++k) {
-        const int x = lane + 32 * k;
-        if (k < nxs && x < L) {
-          const uint32_t v = row[x];
-          if (v) {
-            rsum += v;
-            col[k] += v;
-            pix_add<WIDE>(sm, o[0] + y * L + x, v);                          // (y, x)
-            if (P > 3) pix_add<WIDE>(sm, o[3] + y * F3 + x + z, v);          // (y, x+z)
-            if (P > 4) pix_add<WIDE>(sm, o[4] + y * F3 + x - z + N - 1, v);  // (y, x-z)
-            if (P > 5) pix_atomic<WIDE>(sm, o[5] + (y + z) * L + x, v);      // (y+z, x)
-            if (P > 6) pix_atomic<WIDE>(sm, o[6] + (y - z + N - 1) * L + x, v);
-            if (P > 7) pix_atomic<WIDE>(sm, o[7] + z * F7 + x + y, v);      // (z, x+y)
-            if (P > 8) pix_atomic<WIDE>(sm, o[8] + z * F7 + x - y + M - 1, v);
+  const int slice_bytes = L * M * (int)sizeof(T);
+  const int G = stage_slices(slice_bytes, N);
+  const uintptr_t vbase = reinterpret_cast<uintptr_t>(t.vol);
+  // starts the copy of the stage from slice z0 into buffer buf; returns the
+  // byte offset of slice z0 in the buffer
+  auto fetch = [&](int z0, int buf) -> int {
+    const uintptr_t a = vbase + (uintptr_t)z0 * slice_bytes;
+    const uintptr_t a16 = a & ~(uintptr_t)15;
+    const int hd = (int)(a - a16);
+    const int nb = (hd + min(G, N - z0) * slice_bytes + 15) >> 4;
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(slab + buf * kSlabWords);
+    for (int i = threadIdx.x; i < nb; i += NT)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16 * i),
+                   "l"(a16 + 16 * (uintptr_t)i)
+                   : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    return hd;
+  };
+  const int nc = (L + 3) >> 2, npos = M * nc;
+  const int Zg = t.zblocks[NT == 512 ? 1 : 0];  // z-blocks per stage
+  int head = fetch(0, 0), head_next = 0;
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  for (int z0 = 0, buf = 0; z0 < N; z0 += G, buf ^= 1) {
+    // in flight while this stage is processed: the other buffer was last
+    // read in the previous stage, which ended with a barrier
+    if (z0 + G < N) head_next = fetch(z0 + G, buf ^ 1);
+    const unsigned char* S = reinterpret_cast<const unsigned char*>(slab + buf * kSlabWords);
+    const int gz = min(G, N - z0), zlen = (gz + Zg - 1) / Zg;
+    for (int it = threadIdx.x; it < npos * Zg; it += NT) {
+      const int zg = it / npos, pos = it - zg * npos;
+      const int y = pos / nc, x0 = (pos - y * nc) << 2;
+      const int zs = z0 + zg * zlen, ze = min(z0 + gz, zs + zlen);
+      if (zs >= ze) continue;
+      const int rem = L - x0;
+      // byte offset of the chunk in the stage, and the pixel indices at z = zs
+      int off = head + (((zs - z0) * M + y) * L + x0) * (int)sizeof(T);
+      int b1 = o[1] + zs * M + y, b2 = o[2] + zs * L + x0;
+      int b3 = o[3] + y * F3 + x0 + zs, b4 = o[4] + y * F3 + x0 - zs + N - 1;
+      int b5 = o[5] + (y + zs) * L + x0, b6 = o[6] + (y - zs + N - 1) * L + x0;
+      int b7 = o[7] + zs * F7 + x0 + y, b8 = o[8] + zs * F7 + x0 - y + M - 1;
+      uint32_t i0a = 0, i0b = 0, i0c = 0, i0d = 0;  // image 0 over the block
+      for (int z = zs; z < ze; ++z) {
+        const uint32_t* W = reinterpret_cast<const uint32_t*>(S + (off & ~3));
+        const uint32_t sh = (uint32_t)(off & 3) << 3;
+        uint32_t p01, p23, rs;
+        if constexpr (sizeof(T) == 1) {
+          uint32_t wv = __funnelshift_r(W[0], W[1], sh);
+          if (rem < 4) wv &= (1u << (rem << 3)) - 1u;
+          p01 = __byte_perm(wv, 0u, 0x4140);
+          p23 = __byte_perm(wv, 0u, 0x4342);
+          rs = __dp4a(wv, 0x01010101u, 0u);
+        } else {  // off is even: the volume and its slices are 2-byte aligned
+          const uint32_t w1 = W[1];
+          p01 = __funnelshift_r(W[0], w1, sh);
+          p23 = __funnelshift_r(w1, W[2], sh);
+          if (rem < 4) {
+            if (rem == 1) p01 &= 0xffffu;
+            p23 = rem == 3 ? (p23 & 0xffffu) : 0u;
+          }
+          rs = (p01 & 0xffffu) + (p01 >> 16) + (p23 & 0xffffu) + (p23 >> 16);
+        }
+        if (rs) {
+          pix_atomic<WIDE>(sm, b1, rs);           // (z, y)
+          add4<WIDE>(sm, b2, p01, p23);           // (z, x)
+          if (P > 3) add4<WIDE>(sm, b3, p01, p23);  // (y, x+z)
+          if (P > 4) add4<WIDE>(sm, b4, p01, p23);  // (y, x-z)
+          if constexpr (MANY) {
+            add4<WIDE>(sm, b5, p01, p23);             // (y+z, x)
+            if (P > 6) add4<WIDE>(sm, b6, p01, p23);  // (y-z, x)
+            if (P > 7) add4<WIDE>(sm, b7, p01, p23);  // (z, x+y)
+            if (P > 8) add4<WIDE>(sm, b8, p01, p23);  // (z, x-y)
+          }
+          if constexpr (WIDE) {
+            i0a += p01 & 0xffffu; i0b += p01 >> 16; i0c += p23 & 0xffffu; i0d += p23 >> 16;
+          } else {  // packed: every pixel sum stays below 2^16
+            i0a += p01; i0c += p23;
           }
         }
+        off += slice_bytes;
+        b1 += M; b2 += L; b3 += 1; b4 -= 1;
+        if constexpr (MANY) { b5 += L; b6 -= L; b7 += F7; b8 += F7; }
       }
-      rsum = __reduce_add_sync(0xffffffffu, rsum);
-      if (lane == 0 && rsum) pix_add<WIDE>(sm, o[1] + z * M + y, rsum);  // (z, y)
-      __syncwarp();  // row y's pixels of images 3 and 4 move between lanes with z
+      const int b0 = o[0] + y * L + x0;  // (y, x)
+      if constexpr (WIDE) {
+        atomicAdd(sm + b0, i0a);
+        atomicAdd(sm + b0 + 1, i0b);
+        atomicAdd(sm + b0 + 2, i0c);
+        atomicAdd(sm + b0 + 3, i0d);
+      } else {
+        add4<false>(sm, b0, i0a, i0c);
+      }
     }
-#pragma unroll
-    for (int k = 0; k < kMaxXSlots; ++k) {
-      const int x = lane + 32 * k;
-      if (k < nxs && x < L && col[k]) pix_atomic<WIDE>(sm, o[2] + z * L + x, col[k]);  // (z, x)
-    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    head = head_next;
+    __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------- step 2
 
-__device__ __forceinline__ int64_t shfl_xor_i64(int64_t v, int m) {
+// Geometry of image k (the table of dpma.h): S rows of F pixels, and the
+// offsets that make its coordinates signed (Sec. 5).
+__device__ __forceinline__ void image_geom_dev(const BTask& t, int k, int& S, int& F, int& os, int& of) {
+  const int L = t.L, M = t.M, N = t.N;
+  os = 0;
+  of = 0;
+  switch (k) {
+    case 0: S = M; F = L; break;
+    case 1: S = N; F = M; break;
+    case 2: S = N; F = L; break;
+    case 3: S = M; F = L + N - 1; break;
+    case 4: S = M; F = L + N - 1; of = N - 1; break;
+    case 5: S = M + N - 1; F = L; break;
+    case 6: S = M + N - 1; F = L; os = N - 1; break;
+    case 7: S = N; F = L + M - 1; break;
+    default: S = N; F = L + M - 1; of = M - 1; break;
+  }
+}
+
+// Per-image plan of the moment stage, built once per volume.
+struct ImgMeta {
+  int S, F, os, of;
+  int nseg;    // interleaved segments per row
+  int ustart;  // first unit of the image ([P] = all units)
+};
+
+__device__ __forceinline__ int64_t shfl_xor_v(int64_t v, int m) {
   return __shfl_xor_sync(0xffffffffu, (long long)v, m);
 }
-__device__ __forceinline__ i128 shfl_xor_i128(i128 v, int m) {
+__device__ __forceinline__ i128 shfl_xor_v(i128 v, int m) {
   const uint64_t lo = (uint64_t)v, hi = (uint64_t)((u128)v >> 64);
   const uint64_t l2 = __shfl_xor_sync(0xffffffffu, (unsigned long long)lo, m);
   const uint64_t h2 = __shfl_xor_sync(0xffffffffu, (unsigned long long)hi, m);
   return (i128)(((u128)h2 << 64) | l2);
 }
-template <typename RT>
-__device__ __forceinline__ RT warp_sum(RT v) {
-#pragma unroll
-  for (int m = 16; m >= 1; m >>= 1) {
-    if constexpr (sizeof(RT) == 8) v += shfl_xor_i64(v, m);
-    else v += shfl_xor_i128(v, m);
-  }
-  return v;
-}
 
-// 2-D moments T_ab (a + b <= K, signed coordinates) of one image held in
-// shared memory (Eq. 1): per row s, the power sums R_b(s) = sum_f I f^b, then
-// T_ab = sum_s s^a R_b(s).  Lane j accumulates pairs j and j + 32.
-template <typename RT, bool WIDE, int NT>
-__device__ void image_moments(const uint32_t* sm, int base, int64_t S, int64_t F, int64_t off_s,
-                              int64_t off_f, int K, i128* part, i128* Tout) {
+// 2-D moments T_ab (a + b <= K, signed coordinates) of every image of one
+// volume held in shared memory (Eq. 1 with the origin shift of Sec. 5), in
+// rounds of at most U units:
+//  1. unit u = (image k, row s, segment g): row s of image k is cut into
+//     nseg_k interleaved segments of about Lseg pixels; the unit's partial
+//     power sums R_b = sum over its pixels f of I f^b are stored with s;
+//  2. warp w takes the jobs (k, b) numbered w, w + NW, ...; its lanes run
+//     over image k's units of the round, accumulating s^a R_b for all
+//     a <= K - b along one chain of products, and the warp totals go into
+//     T_ab.
+// RT holds a row power sum exactly, AT a 2-D moment (int64 when the host's
+// bounds allow, int128 otherwise).
+template <typename RT, typename AT, bool WIDE, int NT>
+__device__ __forceinline__ void volume_moments(const BTask& t, const uint32_t* sm, void* scratch,
+                                               i128* Tacc, ImgMeta* meta, i128* Tout) {
   constexpr int NW = NT / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int K = t.K, P = t.P;
   const int npairs = (K + 1) * (K + 2) / 2;
-  // the (a, b) of this lane's pairs
-  int ja[2], jb[2];
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int j = lane + 32 * h;
-    int n = 0;
-    while ((n + 1) * (n + 2) / 2 <= j) ++n;
-    ja[h] = n - (j - n * (n + 1) / 2);
-    jb[h] = n - ja[h];
+  const int stride = K + 1;  // RT words per unit
+  constexpr int kScratch = 2 * kSlabWords * 4;
+  const int U = min(NT, (int)(kScratch / (stride * (int)sizeof(RT) + 4)));
+  RT* Rs = static_cast<RT*>(scratch);
+  int* Ss = reinterpret_cast<int*>(Rs + (size_t)U * stride);
+  if (threadIdx.x == 0) {
+    int64_t pixels = 0;
+    for (int k = 0; k < P; ++k) {
+      ImgMeta& m = meta[k];
+      image_geom_dev(t, k, m.S, m.F, m.os, m.of);
+      pixels += (int64_t)m.S * m.F;
+    }
+    // segment length: all pixels over about U units
+    const int Lseg = (int)(pixels > 4ll * U ? (pixels + U - 1) / U : 4);
+    int u = 0;
+    for (int k = 0; k < P; ++k) {
+      meta[k].nseg = (meta[k].F + Lseg - 1) / Lseg;
+      meta[k].ustart = u;
+      u += meta[k].S * meta[k].nseg;
+    }
+    meta[P].ustart = u;
   }
-  i128 acc[2] = {0, 0};
-  for (int64_t s = warp; s < S; s += NW) {
-    RT R[kMaxK + 1];
+  for (int j = threadIdx.x; j < P * npairs; j += NT) Tacc[j] = 0;
+  __syncthreads();
+  const int units = meta[P].ustart;
+  for (int u0 = 0; u0 < units; u0 += U) {
+    const int nu = min(U, units - u0);
+    if ((int)threadIdx.x < nu) {
+      int v = u0 + (int)threadIdx.x, k = 0;
+      while (v >= meta[k + 1].ustart) ++k;
+      const ImgMeta m = meta[k];
+      v -= m.ustart;
+      const int s = v / m.nseg, g = v - s * m.nseg;
+      RT R[kMaxK + 1];
 #pragma unroll
-    for (int b = 0; b <= kMaxK; ++b) R[b] = 0;
-    for (int64_t f = lane; f < F; f += 32) {
-      const uint32_t v = pix_get<WIDE>(sm, base + (int)(s * F + f));
-      if (v) {
-        const RT fs = (RT)(f - off_f);
-        RT pw = (RT)v;
+      for (int b = 0; b <= kMaxK; ++b) R[b] = 0;
+      const int row = t.img_off[k] + s * m.F;
+      for (int f = g; f < m.F; f += m.nseg) {
+        const uint32_t pv = pix_get<WIDE>(sm, row + f);
+        if (pv) {
+          const RT fs = (RT)(f - m.of);
+          RT pw = (RT)pv;
+          R[0] += pw;
 #pragma unroll
-        for (int b = 0; b <= kMaxK; ++b) {
-          if (b > K) break;
-          R[b] += pw;
-          pw *= fs;
+          for (int b = 1; b <= kMaxK; ++b) {
+            if (b > K) break;
+            pw *= fs;
+            R[b] += pw;
+          }
         }
       }
-    }
-    bool any = false;
+      RT* dst = Rs + (size_t)threadIdx.x * stride;
 #pragma unroll
-    for (int b = 0; b <= kMaxK; ++b) {
-      if (b > K) break;
-      R[b] = warp_sum<RT>(R[b]);
-      any = any || R[b] != 0;
+      for (int b = 0; b <= kMaxK; ++b) {
+        if (b > K) break;
+        dst[b] = R[b];
+      }
+      Ss[threadIdx.x] = s - m.os;
     }
-    if (!any) continue;
-    const i128 ss = (i128)(s - off_s);
+    __syncthreads();
+    for (int job = warp; job < P * (K + 1); job += NW) {
+      const int k = job / (K + 1), b = job - k * (K + 1);
+      const int lo = max(meta[k].ustart - u0, 0), hi = min(meta[k + 1].ustart - u0, nu);
+      if (lo >= hi) continue;  // uniform across the warp
+      AT acc[kMaxK + 1];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      if (lane + 32 * h >= npairs) continue;
-      i128 sp = 1;
-      for (int a = 0; a < ja[h]; ++a) sp *= ss;
-      RT rb = 0;
+      for (int a = 0; a <= kMaxK; ++a) acc[a] = 0;
+      for (int u = lo + lane; u < hi; u += 32) {
+        const RT r = Rs[(size_t)u * stride + b];
+        if (r == 0) continue;
+        AT pw = (AT)r;
+        const int64_t sv = Ss[u];
+        acc[0] += pw;
 #pragma unroll
-      for (int b = 0; b <= kMaxK; ++b)
-        if (b == jb[h]) rb = R[b];
-      acc[h] += sp * (i128)rb;
+        for (int a = 1; a <= kMaxK; ++a) {
+          if (a > K - b) break;
+          pw *= sv;
+          acc[a] += pw;
+        }
+      }
+#pragma unroll
+      for (int a = 0; a <= kMaxK; ++a) {
+        if (a > K - b) break;
+#pragma unroll
+        for (int mk = 16; mk >= 1; mk >>= 1) acc[a] += shfl_xor_v(acc[a], mk);
+        // pair (a, b) is number n (n + 1) / 2 + b with n = a + b
+        if (lane == 0) Tacc[k * npairs + (a + b) * (a + b + 1) / 2 + b] += (i128)acc[a];
+      }
     }
+    __syncthreads();
   }
-#pragma unroll
-  for (int h = 0; h < 2; ++h)
-    if (lane + 32 * h < npairs) part[warp * kMax2D + lane + 32 * h] = acc[h];
-  __syncthreads();
-  for (int j = threadIdx.x; j < npairs; j += NT) {
-    i128 sum = 0;
-    for (int w = 0; w < NW; ++w) sum += part[w * kMax2D + j];
-    Tout[j] = sum;
-  }
-  __syncthreads();
+  for (int j = threadIdx.x; j < P * npairs; j += NT) Tout[j] = Tacc[j];
 }
 
 template <typename T, bool WIDE, int NT>
-__device__ void run_task(const BTask& t, uint32_t* sm, i128* part, i128* Tout) {
-  project_volume<T, WIDE, NT>(t, sm);
-  __syncthreads();
-  const int npairs = (t.K + 1) * (t.K + 2) / 2;
-  for (int k = 0; k < t.P; ++k) {
-    // geometry of image k (the table of dpma.h)
-    const int64_t L = t.L, M = t.M, N = t.N;
-    int64_t S, F, os = 0, of = 0;
-    switch (k) {
-      case 0: S = M; F = L; break;
-      case 1: S = N; F = M; break;
-      case 2: S = N; F = L; break;
-      case 3: S = M; F = L + N - 1; break;
-      case 4: S = M; F = L + N - 1; of = N - 1; break;
-      case 5: S = M + N - 1; F = L; break;
-      case 6: S = M + N - 1; F = L; os = N - 1; break;
-      case 7: S = N; F = L + M - 1; break;
-      default: S = N; F = L + M - 1; of = M - 1; break;
-    }
-    if (t.r64) image_moments<int64_t, WIDE, NT>(sm, t.img_off[k], S, F, os, of, t.K, part, Tout + k * npairs);
-    else image_moments<i128, WIDE, NT>(sm, t.img_off[k], S, F, os, of, t.K, part, Tout + k * npairs);
-  }
+__device__ __forceinline__ void project_any(const BTask& t, uint32_t* sm, uint32_t* slab) {
+  if (t.P > 5) project_volume<T, WIDE, true, NT>(t, sm, slab);
+  else project_volume<T, WIDE, false, NT>(t, sm, slab);
+}
+
+template <bool WIDE, int NT>
+__device__ __forceinline__ void moments_any(const BTask& t, const uint32_t* sm, uint32_t* slab,
+                                            i128* Tacc, ImgMeta* meta, i128* Tout) {
+  if (t.r64 && t.t64) volume_moments<int64_t, int64_t, WIDE, NT>(t, sm, slab, Tacc, meta, Tout);
+  else if (t.r64) volume_moments<int64_t, i128, WIDE, NT>(t, sm, slab, Tacc, meta, Tout);
+  else volume_moments<i128, i128, WIDE, NT>(t, sm, slab, Tacc, meta, Tout);
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT) batch_fused_kernel(FusedParams p) {
+__global__ void __launch_bounds__(NT, 1) batch_fused_kernel(FusedParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  i128* part = reinterpret_cast<i128*>(smem_raw);
-  uint32_t* sm = reinterpret_cast<uint32_t*>(smem_raw + kPartBytes);
+  i128* Tacc = reinterpret_cast<i128*>(smem_raw);
+  __shared__ ImgMeta meta[kMaxImages + 1];
+  uint32_t* slab = reinterpret_cast<uint32_t*>(smem_raw + kPartBytes);  // [2][kSlabWords]
+  uint32_t* sm = slab + 2 * kSlabWords;                                  // images
   __shared__ int s_task;
   for (;;) {
     if (threadIdx.x == 0) s_task = atomicAdd(p.counter, 1);
@@ -259,17 +410,19 @@ __global__ void __launch_bounds__(NT) batch_fused_kernel(FusedParams p) {
     const int ti = s_task;
     if (ti >= p.ntasks) break;
     const BTask t = p.tasks[p.order[ti]];
-    for (int w = threadIdx.x; w < t.words; w += NT) sm[w] = 0;
+    for (int w = threadIdx.x; w < t.words + kSlackWords; w += NT) sm[w] = 0;
     __syncthreads();
     i128* Tout = p.T + t.t_off;
     if (t.dtype == DPMA_U8) {
-      if (t.wide) run_task<uint8_t, true, NT>(t, sm, part, Tout);
-      else run_task<uint8_t, false, NT>(t, sm, part, Tout);
+      if (t.wide) project_any<uint8_t, true, NT>(t, sm, slab);
+      else project_any<uint8_t, false, NT>(t, sm, slab);
     } else {
-      if (t.wide) run_task<uint16_t, true, NT>(t, sm, part, Tout);
-      else run_task<uint16_t, false, NT>(t, sm, part, Tout);
+      if (t.wide) project_any<uint16_t, true, NT>(t, sm, slab);
+      else project_any<uint16_t, false, NT>(t, sm, slab);
     }
-    // run_task ends with a barrier: s_task may be rewritten
+    if (t.wide) moments_any<true, NT>(t, sm, slab, Tacc, meta, Tout);
+    else moments_any<false, NT>(t, sm, slab, Tacc, meta, Tout);
+    __syncthreads();  // s_task, the images and the scratch area are rewritten next
   }
 }
 
@@ -440,7 +593,7 @@ void classify(const dpma_volume_desc* descs, int count, Classified* c) {
   for (int i = 0; i < count; ++i) {
     const dpma_volume_desc& d = descs[i];
     const int P = num_images(d.K);
-    bool fused = d.dtype != DPMA_F32 && d.L <= 32 * kMaxXSlots;
+    bool fused = d.dtype != DPMA_F32;
     BTask t{};
     if (fused) {
       const double vmax = d.dtype == DPMA_U8 ? 255.0 : 65535.0;
@@ -455,16 +608,37 @@ void classify(const dpma_volume_desc* descs, int count, Classified* c) {
         maxF = std::max(maxF, std::max(g.F, g.S));
       }
       const int64_t words = t.wide ? pix : pix / 2;
-      if (pix > (1ll << 30) || (size_t)words * 4 + kPartBytes > (size_t)kSmemLimit) fused = false;
+      // one slice with its 16-byte alignment head and the two words a chunk
+      // load may read past it fits in one stage buffer
+      const int64_t slice_b = d.L * d.M * (int64_t)(d.dtype == DPMA_U8 ? 1 : 2);
+      if (pix > (1ll << 30) || slice_b + 30 > (int64_t)(kSlabWords - 8) * 4 ||
+          (size_t)(words + kSlackWords) * 4 + kPartBytes + 2 * kSlabWords * 4 > (size_t)kSmemLimit)
+        fused = false;
       if (fused) {
         t.vol = d.volume;
         t.L = (int)d.L; t.M = (int)d.M; t.N = (int)d.N;
         t.dtype = d.dtype; t.K = d.K; t.P = P;
         t.words = (int)words;
+        // z-blocks per stage: the fewest chunk loads on the busiest thread,
+        // counting two loads of overhead per work item
+        const int64_t slice_bytes = d.L * d.M * (int64_t)(d.dtype == DPMA_U8 ? 1 : 2);
+        const int64_t G = stage_slices(slice_bytes, (int)d.N);
+        const int64_t npos = d.M * ((d.L + 3) / 4);
+        for (int v = 0; v < 2; ++v) {
+          const int64_t nt = v ? 512 : 256;
+          int64_t best = -1, bz = 1;
+          for (int64_t zg = 1; zg <= std::min<int64_t>(G, 32); ++zg) {
+            const int64_t cost = ((npos * zg + nt - 1) / nt) * ((G + zg - 1) / zg + 2);
+            if (best < 0 || cost < best) { best = cost; bz = zg; }
+          }
+          t.zblocks[v] = (int)bz;
+        }
         // a row power sum is at most (vmax * line) * maxF^K * maxF
         const double bits = std::log2(vmax * (double)line + 1) + d.K * std::log2((double)maxF + 1) +
                             std::log2((double)maxF + 1);
         t.r64 = bits < 62.0 ? 1 : 0;
+        // every 2-D moment and partial sum of absolute terms fits int64
+        t.t64 = log2_bound_2d(d.L, d.M, d.N, vmax, d.K) < 62.0 ? 1 : 0;
         t.t_off = c->t_total;
         t.out_off = d.out_offset;
         c->t_total += (int64_t)P * num_2d(d.K);
@@ -487,7 +661,9 @@ std::vector<int> lpt_order(const std::vector<BTask>& tasks) {
   return order;
 }
 
-size_t fused_smem(size_t max_words) { return (size_t)kPartBytes + max_words * 4; }
+size_t fused_smem(size_t max_words) {
+  return (size_t)kPartBytes + 2 * (size_t)kSlabWords * 4 + (max_words + kSlackWords) * 4;
+}
 
 int fused_grid(size_t smem, int threads, int ntasks) {
   int dev = 0, sms = 0, per_sm = 0;

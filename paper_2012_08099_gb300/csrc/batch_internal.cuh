@@ -16,7 +16,9 @@ struct BTask {
   int dtype, K, P;
   int wide;   // 1: 32-bit pixels, 0: 16-bit pixels
   int r64;    // 1: row power sums fit int64
+  int t64;    // 1: 2-D moments fit int64
   int words;  // 32-bit words of shared memory the images take
+  int zblocks[2];  // z-blocks per projection stage at 256 and 512 threads
   int img_off[kMaxImages];  // first pixel of each image (even, in pixel units)
   int64_t t_off;            // first 2-D moment of this volume in T (int128 units)
   int64_t out_off;          // byte offset of this volume's moments in the output

@@ -37,7 +37,7 @@ def dev(vol):
 
 def mixed_batch():
     """ROI masks plus odd sizes, orders 0..8, 16- and 32-bit pixels, and volumes
-    that take the single-volume path (float32, L > 256)."""
+    that take the single-volume path (float32, a z-slice over 24 KB)."""
     vols, Ks = [], []
     for v in synth.roi_batch(40, seed=11).volumes:
         vols.append(v)
@@ -47,7 +47,8 @@ def mixed_batch():
         ((1, 1, 1), np.uint16, 0), ((2, 3, 1), np.uint8, 2), ((5, 7, 256), np.uint16, 5),
         ((12, 13, 14), np.uint8, 7), ((30, 20, 10), np.uint8, 8), ((64, 64, 64), np.uint8, 4),
         ((300, 4, 4), np.uint8, 4), ((4, 4, 300), np.uint16, 4), ((10, 11, 12), np.float32, 6),
-        ((3, 1, 257), np.uint8, 3), ((1, 96, 1), np.uint8, 1),
+        ((3, 1, 257), np.uint8, 3), ((1, 96, 1), np.uint8, 1), ((3, 100, 300), np.uint16, 4),
+        ((7, 3, 255), np.uint8, 6), ((2, 5, 254), np.uint16, 8),
     ]
     for i, (shape, dt, K) in enumerate(cases):
         vols.append(synth.uniform_volume(shape, dt, seed=100 + i))
@@ -69,8 +70,8 @@ def test_batched_matches_single_volume(dpma):
     vols, Ks = mixed_batch()
     tv = [dev(v) for v in vols]
     b = dpma.Batch([t for t, _ in tv], Ks, [d for _, d in tv])
-    assert b.info(1) == 3                  # float32 and the two volumes with L > 256
-    assert b.info(0) == len(vols) - 3      # every other volume is fused
+    assert b.info(1) == 2                  # float32 and the 60 KB slices
+    assert b.info(0) == len(vols) - 2      # every other volume is fused
     out = b.out_buffer()
     b.run(out)
     b.status()
@@ -81,7 +82,7 @@ def test_batched_matches_single_volume(dpma):
 
 def test_batched_matches_oracle(dpma):
     vols, Ks = mixed_batch()
-    pick = [0, 7, 39, 40, 41, 42, 45, 46, 47, 48]
+    pick = [0, 7, 39, 40, 41, 42, 45, 46, 47, 48, 50, 52, 55, 56]
     vs = [vols[i] for i in pick]
     ks = [Ks[i] for i in pick]
     tv = [dev(v) for v in vs]
