@@ -431,8 +431,13 @@ __global__ void __launch_bounds__(NT, 1) batch_fused_kernel(FusedParams p) {
 struct BCombParams {
   const BTask* tasks;
   int ntasks;
+  int stride;                  // moments per task slot (those of the highest order)
   const int64_t* plans;        // packed plans of every K present
   int off[kMaxK + 1][kMaxK + 1];  // off[K][n]: word offset of degree n of order K
+  // divisor D of degree n of order K as odd << shift, with the inverse of odd
+  // modulo 2^128 (two words, low first)
+  int dshift[kMaxK + 1][kMaxK + 1];
+  uint64_t dinv[kMaxK + 1][kMaxK + 1][2];
   const i128* T;
   unsigned char* out;
   int* status;
@@ -473,31 +478,28 @@ __device__ __forceinline__ void mac256(I256& a, int64_t c, i128 t) {
   if (neg) neg256(prod);
   add256(a, prod);
 }
-// q = a / d exactly; false on a remainder or if q leaves int128
-__device__ bool div256_exact(I256 a, int64_t d, i128* q) {
-  const bool neg = (a.w[3] >> 63) != 0;
-  if (neg) neg256(a);
-  uint64_t qw[4];
-  u128 rem = 0;
-  for (int i = 3; i >= 0; --i) {
-    const u128 cur = (rem << 64) | a.w[i];
-    qw[i] = (uint64_t)(cur / (uint64_t)d);
-    rem = cur % (uint64_t)d;
-  }
-  if (rem != 0 || qw[3] != 0 || qw[2] != 0) return false;
-  const u128 mag = ((u128)qw[1] << 64) | qw[0];
-  if (!neg && (mag >> 127)) return false;
-  if (neg && mag > ((u128)1 << 127)) return false;
-  *q = neg ? (i128)(~mag + 1) : (i128)mag;
+// q = a / d exactly for d = odd << sh (sh < 64): the candidate q is the low
+// 128 bits of (a >> sh) times the inverse of odd modulo 2^128, which is the
+// quotient whenever the division is exact; q * d == a (in 256 bits) holds
+// exactly then, so a remainder or a quotient outside int128 fails the check.
+__device__ bool div_exact(const I256& a, int64_t d, int sh, u128 inv, i128* q) {
+  const u128 lo = ((u128)a.w[1] << 64) | a.w[0];
+  const u128 hi = ((u128)a.w[3] << 64) | a.w[2];
+  const u128 as = sh ? ((lo >> sh) | (hi << (128 - sh))) : lo;
+  const i128 qc = (i128)(as * inv);
+  I256 chk = {{0, 0, 0, 0}};
+  mac256(chk, d, qc);
+  if (chk.w[0] != a.w[0] || chk.w[1] != a.w[1] || chk.w[2] != a.w[2] || chk.w[3] != a.w[3])
+    return false;
+  *q = qc;
   return true;
 }
 
 // One thread per (volume, moment): M = (C t_sel) / D for the moment's degree.
 __global__ void batch_combine_kernel(BCombParams p) {
-  constexpr int kStride = 165;  // moments of order 8
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t ti = gid / kStride;
-  const int m = (int)(gid % kStride);
+  const int64_t ti = gid / p.stride;
+  const int m = (int)(gid % p.stride);
   if (ti >= p.ntasks) return;
   const BTask& t = p.tasks[ti];
   const int K = t.K;
@@ -520,7 +522,8 @@ __global__ void batch_combine_kernel(BCombParams p) {
     mac256(acc, C[row * nm + j], T[img[j] * npairs + pair]);
   }
   i128 q = 0;
-  if (!div256_exact(acc, D, &q)) {
+  const u128 inv = ((u128)p.dinv[K][n][1] << 64) | p.dinv[K][n][0];
+  if (!div_exact(acc, D, p.dshift[K][n], inv, &q)) {
     atomicMax(p.status, kStatusInternal);
     q = 0;
   }
@@ -551,6 +554,8 @@ cudaError_t set_smem(size_t smem) {
 struct DevPlans {
   int64_t* words = nullptr;
   int off[kMaxK + 1][kMaxK + 1] = {};
+  int dshift[kMaxK + 1][kMaxK + 1] = {};
+  uint64_t dinv[kMaxK + 1][kMaxK + 1][2] = {};
 };
 std::mutex g_plans_mu;
 std::vector<DevPlans> g_plans;  // per device
@@ -570,6 +575,20 @@ cudaError_t plans_for_device(const DevPlans** out) {
       const size_t n = pack_combine_plan(K, w.data(), w.size(), off);
       if (n == 0) return cudaErrorInvalidValue;
       for (int d = 0; d <= kMaxK; ++d) dp.off[K][d] = (int)words.size() + off[d];
+      for (int d = 0; d <= K; ++d) {
+        // D = odd << shift; the inverse of odd modulo 2^128 by Newton's
+        // iteration x <- x (2 - odd x), exact to 3 bits at x = odd
+        uint64_t D = (uint64_t)w[off[d]];
+        if (D == 0) return cudaErrorInvalidValue;
+        int sh = 0;
+        while ((D & 1) == 0) { D >>= 1; ++sh; }
+        const u128 odd = D;
+        u128 x = odd;
+        for (int it = 0; it < 7; ++it) x *= (u128)2 - odd * x;
+        dp.dshift[K][d] = sh;
+        dp.dinv[K][d][0] = (uint64_t)x;
+        dp.dinv[K][d][1] = (uint64_t)(x >> 64);
+      }
       words.insert(words.end(), w.begin(), w.begin() + n);
     }
     int64_t* dw = nullptr;
@@ -645,6 +664,7 @@ void classify(const dpma_volume_desc* descs, int count, Classified* c) {
         c->tasks.push_back(t);
         c->fused_index.push_back(i);
         c->max_words = std::max(c->max_words, (size_t)words);
+        c->max_K = std::max(c->max_K, d.K);
       }
     }
     if (!fused) c->single.push_back(i);
@@ -686,9 +706,9 @@ cudaError_t prepare_plans() {
   return plans_for_device(&dp);
 }
 
-cudaError_t enqueue_fused(const BTask* d_tasks, const int* d_order, int n, int* d_counter,
-                          i128* d_T, size_t smem, int threads, int grid, void* out,
-                          int* d_status, cudaStream_t st) {
+cudaError_t enqueue_fused(const BTask* d_tasks, const int* d_order, int n, int max_K,
+                          int* d_counter, i128* d_T, size_t smem, int threads, int grid,
+                          void* out, int* d_status, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const DevPlans* dp = nullptr;
   cudaError_t e = plans_for_device(&dp);
@@ -713,12 +733,15 @@ cudaError_t enqueue_fused(const BTask* d_tasks, const int* d_order, int n, int* 
   BCombParams cp{};
   cp.tasks = d_tasks;
   cp.ntasks = n;
+  cp.stride = (int)num_moments(max_K);
   cp.plans = dp->words;
   std::memcpy(cp.off, dp->off, sizeof(cp.off));
+  std::memcpy(cp.dshift, dp->dshift, sizeof(cp.dshift));
+  std::memcpy(cp.dinv, dp->dinv, sizeof(cp.dinv));
   cp.T = d_T;
   cp.out = static_cast<unsigned char*>(out);
   cp.status = d_status;
-  const int64_t nt = 128, total = (int64_t)n * 165;
+  const int64_t nt = 128, total = (int64_t)n * cp.stride;
   batch_combine_kernel<<<(unsigned)((total + nt - 1) / nt), (unsigned)nt, 0, st>>>(cp);
   return cudaGetLastError();
 }
@@ -768,7 +791,7 @@ dpma_status enqueue_batch(dpma_batch* b, void* out, cudaStream_t st, bool single
   if (n > 0) {
     e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st);
     if (e == cudaSuccess)
-      e = batch::enqueue_fused(b->d_tasks, b->d_order, n, b->d_counter, b->d_T, b->smem,
+      e = batch::enqueue_fused(b->d_tasks, b->d_order, n, b->cls.max_K, b->d_counter, b->d_T, b->smem,
                                b->threads, b->grid, out, b->d_status, st);
     if (e != cudaSuccess)
       return bfail(DPMA_ERR_CUDA, std::string("batched kernels: ") + cudaGetErrorString(e));

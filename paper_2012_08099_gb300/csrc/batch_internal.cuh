@@ -30,10 +30,11 @@ struct Classified {
   std::vector<int> single;        // descriptors for the single-volume path
   int64_t t_total = 0;            // int128 2-D moments of all tasks
   size_t max_words = 0;           // largest image footprint in 32-bit words
+  int max_K = 0;                  // highest order among the fused tasks
 };
 
-// Sorts valid descriptors into fused tasks (integer volumes, L <= 256, images
-// within shared memory) and single-volume ones.  Host only.
+// Sorts valid descriptors into fused tasks (integer volumes whose z-slice and
+// images fit in shared memory) and single-volume ones.  Host only.
 void classify(const dpma_volume_desc* d, int n, Classified* c);
 // Processing order of the fused queue: largest volumes first.
 std::vector<int> lpt_order(const std::vector<BTask>& tasks);
@@ -45,12 +46,13 @@ int fused_grid(size_t smem, int threads, int ntasks);
 // (built once per device; synchronous the first time).
 cudaError_t prepare_plans();
 // Enqueues the fused projection + 2-D moment launch and the batched combine
-// for n tasks already in device memory; `out` is the base the tasks' out_off
-// refer to; *d_status becomes 7 if an exact division left a remainder.
-// d_counter must be zero when the launch starts (the caller clears it).
-cudaError_t enqueue_fused(const BTask* d_tasks, const int* d_order, int n, int* d_counter,
-                          i128* d_T, size_t smem, int threads, int grid, void* out,
-                          int* d_status, cudaStream_t st);
+// for n tasks already in device memory, whose highest order is max_K; `out`
+// is the base the tasks' out_off refer to; *d_status becomes 7 if an exact
+// division left a remainder.  d_counter must be zero when the launch starts
+// (the caller clears it).
+cudaError_t enqueue_fused(const BTask* d_tasks, const int* d_order, int n, int max_K,
+                          int* d_counter, i128* d_T, size_t smem, int threads, int grid,
+                          void* out, int* d_status, cudaStream_t st);
 // Enqueues *dst = max(*dst, *src) on the device.
 cudaError_t enqueue_merge_status(const int* src, int* dst, cudaStream_t st);
 

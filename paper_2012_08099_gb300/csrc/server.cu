@@ -427,7 +427,7 @@ bool launch_group(dpma_server* s, Group* g, bool fused) {
       const size_t smem = batch::fused_smem(c.max_words);
       const int grid = batch::fused_grid(smem, 512, n);
       e = batch::enqueue_fused(reinterpret_cast<const BTask*>(cdev),
-                               reinterpret_cast<const int*>(cdev + tb), n,
+                               reinterpret_cast<const int*>(cdev + tb), n, c.max_K,
                                reinterpret_cast<int*>(cdev + tb + ob),
                                reinterpret_cast<i128*>(base), smem, 512, grid, base,
                                reinterpret_cast<int*>(cdev + tb + ob + 256), st);
