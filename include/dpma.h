@@ -146,7 +146,11 @@ dpma_status dpma_moments_async(const void* volume, int64_t L, int64_t M, int64_t
  * End to end from host memory: copies the volume host->device, computes,
  * copies the moments device->host, and returns when `host_out` holds them.
  * `host_volume` and `host_out` are host pointers; device buffers are owned
- * and reused by the library.
+ * and reused by the library.  The volume is copied in z-chunks (about 4 MB,
+ * at most 16) on a separate stream, and the projection of each chunk runs
+ * while the next one is copied; pinned host memory gives the full link rate.
+ * Float results may differ from the device-resident call in the last bits
+ * (partial sums merge in another order), within the library's tolerance.
  */
 dpma_status dpma_moments_host(const void* host_volume, int64_t L, int64_t M, int64_t N,
                               dpma_dtype dtype, int K, void* host_out);

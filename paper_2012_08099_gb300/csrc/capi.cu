@@ -92,6 +92,8 @@ struct DeviceState {
   void* host_vol = nullptr;  // device buffers of dpma_moments_host
   size_t host_vol_bytes = 0;
   void* host_out = nullptr;
+  cudaStream_t copy_stream = nullptr;  // host-to-device chunks of dpma_moments_host
+  cudaEvent_t chunk_ready = nullptr;
 };
 
 std::mutex g_states_mu;
@@ -176,8 +178,25 @@ struct StageRecorder {
 };
 
 // Enqueue the three steps on `st` with workspace `ws` (layout `w`).
+size_t elem_size(dpma_dtype d) { return d == DPMA_U8 ? 1 : (d == DPMA_U16 ? 2 : 4); }
+
+// Host volumes arrive in z-chunks: about 4 MB each, at most 16.
+int64_t host_chunk_slices(int64_t N, size_t vbytes) {
+  int64_t n = (int64_t)(vbytes / (4u << 20));
+  n = n < 1 ? 1 : (n > 16 ? 16 : n);
+  if (n > N) n = N;
+  return (N + n - 1) / n;
+}
+
+// The pipeline on stream st.  With a host source (host_src non-null) the
+// volume is copied into `volume` in z-chunks on copy_st, and the projection
+// of each chunk starts as soon as its copy has landed, so the copy of the
+// next chunk overlaps it; launches over disjoint z-ranges add up to the
+// images of the whole volume.
 dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dtype dtype, int K,
-                    void* out, cudaStream_t st, unsigned char* ws, const Layout& w) {
+                    void* out, cudaStream_t st, unsigned char* ws, const Layout& w,
+                    const void* host_src = nullptr, cudaStream_t copy_st = nullptr,
+                    cudaEvent_t ev = nullptr) {
   cudaError_t e = prepare_combine(K);
   if (e != cudaSuccess) return cuda_fail(e, "combine plan");
   StageRecorder rec(st);
@@ -195,8 +214,30 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
   a.images = images;
   a.set = w.set;
   a.status = reinterpret_cast<int*>(ws + w.off_status);
-  e = launch_project(a, st);
-  if (e != cudaSuccess) return cuda_fail(e, "projection kernel");
+  if (host_src) {
+    const size_t slice = (size_t)L * M * elem_size(dtype);
+    const int64_t zc = host_chunk_slices(N, slice * N);
+    // the staging buffer is rewritten only after all earlier work on st
+    e = cudaEventRecord(ev, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(copy_st, ev, 0);
+    for (int64_t z0 = 0; z0 < N && e == cudaSuccess; z0 += zc) {
+      const int64_t nz = (N - z0) < zc ? (N - z0) : zc;
+      e = cudaMemcpyAsync(static_cast<unsigned char*>(const_cast<void*>(volume)) + z0 * slice,
+                          static_cast<const unsigned char*>(host_src) + z0 * slice, nz * slice,
+                          cudaMemcpyHostToDevice, copy_st);
+      if (e == cudaSuccess) e = cudaEventRecord(ev, copy_st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+      if (e != cudaSuccess) return cuda_fail(e, "copy volume chunk to device");
+      a.z0 = z0;
+      a.nz = nz;
+      e = launch_project(a, st);
+      if (e != cudaSuccess) return cuda_fail(e, "projection kernel");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "copy volume to device");
+  } else {
+    e = launch_project(a, st);
+    if (e != cudaSuccess) return cuda_fail(e, "projection kernel");
+  }
   rec.mark(1);
   const bool fl = is_float(dtype);
   e = launch_image_moments(images, w.set, K, fl, ws + w.off_part, ws + w.off_m2d, st);
@@ -207,8 +248,6 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
   rec.mark(3);
   return DPMA_OK;
 }
-
-size_t elem_size(dpma_dtype d) { return d == DPMA_U8 ? 1 : (d == DPMA_U16 ? 2 : 4); }
 
 }  // namespace
 
@@ -350,10 +389,17 @@ dpma_status dpma_moments_host(const void* host_volume, int64_t L, int64_t M, int
   ds->host_out = static_cast<unsigned char*>(ds->host_vol) + align_up(vbytes, 256);
   e = ensure_buffer(&ds->ws, &ds->ws_bytes, w.total);
   if (e != cudaSuccess) return cuda_fail(e, "workspace");
-  e = cudaMemcpyAsync(ds->host_vol, host_volume, vbytes, cudaMemcpyHostToDevice, ds->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "copy volume to device");
+  if (!ds->copy_stream) {
+    e = cudaStreamCreateWithFlags(&ds->copy_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "copy stream");
+  }
+  if (!ds->chunk_ready) {
+    e = cudaEventCreateWithFlags(&ds->chunk_ready, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "chunk event");
+  }
   unsigned char* ws = static_cast<unsigned char*>(ds->ws);
-  s = enqueue(ds->host_vol, L, M, N, dtype, K, ds->host_out, ds->stream, ws, w);
+  s = enqueue(ds->host_vol, L, M, N, dtype, K, ds->host_out, ds->stream, ws, w, host_volume,
+              ds->copy_stream, ds->chunk_ready);
   if (s != DPMA_OK) return s;
   const size_t out_bytes = (size_t)num_moments(K) * (is_float(dtype) ? 8 : 16);
   int status = 0;

@@ -71,6 +71,9 @@ struct ProjectArgs {
   void* images;
   ImageSet set;
   int* status;  // device status word for bounded-wait timeouts (may be null)
+  // slices z0 .. z0 + nz - 1 only (nz = 0: the whole volume); the images
+  // are accumulated, so launches over disjoint ranges add up to the volume
+  int64_t z0 = 0, nz = 0;
 };
 
 // Step 1: images must be zeroed by the caller (the launcher does not clear).

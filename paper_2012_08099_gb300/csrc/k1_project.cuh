@@ -79,8 +79,9 @@ template <typename T, int P> struct TileCfg {
 struct K1Params {
   const void* vol;
   int64_t L, M, N;
+  int64_t z0, nz;  // the launch projects slices z0 .. z0 + nz - 1
   int64_t nbands, nxt;
-  int64_t units;  // nxt * nbands * N
+  int64_t units;  // nxt * nbands * nz
   int64_t cpt;    // CTAs per x-tile (grid = nxt * cpt), or 0: contiguous ranges
   ImageSet set;
   void* images;
@@ -368,7 +369,7 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
   int64_t ub, ue;
   if (p.cpt > 0) {
     const int64_t tile = blockIdx.x % p.nxt, c = blockIdx.x / p.nxt;
-    const int64_t W = p.nbands * p.N;
+    const int64_t W = p.nbands * p.nz;
     ub = tile * W + W * c / p.cpt;
     ue = tile * W + W * (c + 1) / p.cpt;
   } else {
@@ -386,9 +387,10 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
   __syncthreads();
 
   // unit -> (tile x0, band y0, z); units run z fastest, then band, then tile
+  const int64_t zbeg = p.z0, zend = p.z0 + p.nz;
   auto decode = [&](int64_t u, int64_t& x0, int64_t& y0, int64_t& z) {
-    const int64_t seg = u / N;
-    z = u % N;
+    const int64_t seg = u / p.nz;
+    z = zbeg + u % p.nz;
     y0 = (seg % p.nbands) * BY;
     x0 = (seg / p.nbands) * XT;
   };
@@ -405,8 +407,8 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
       mbar_expect_tx(mb, (uint32_t)C::SLICE);
       tma_load_3d(smem_u32(stage + (size_t)st * BY * XT), &vmap, (int)pc_x0, (int)pc_y0,
                   (int)pc_z, mb);
-      if (++pc_z == N) {
-        pc_z = 0;
+      if (++pc_z == zend) {
+        pc_z = zbeg;
         pc_y0 += BY;
         if (pc_y0 >= M) { pc_y0 = 0; pc_x0 += XT; }
       }
@@ -608,7 +610,7 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
     // one segment: a (tile, band) streamed over z in [za, zb)
     int64_t x0, y0, za;
     decode(u, x0, y0, za);
-    const int64_t zb = (N - za) < (ue - u) ? N : za + (ue - u);
+    const int64_t zb = (zend - za) < (ue - u) ? zend : za + (ue - u);
     const int64_t xs = x0 + xl, yt = y0 + yl;
     // which of the thread's rows and columns hold voxels
     const int ncol = (int)((L - xs) <= 0 ? 0 : ((L - xs) < R ? (L - xs) : R));
@@ -1057,9 +1059,11 @@ cudaError_t launch_t(const ProjectArgs& a, cudaStream_t st) {
   K1Params p{};
   p.vol = a.vol;
   p.L = a.L; p.M = a.M; p.N = a.N;
+  p.z0 = a.nz > 0 ? a.z0 : 0;
+  p.nz = a.nz > 0 ? a.nz : a.N;
   p.nbands = (a.M + BY - 1) / BY;
   p.nxt = (a.L + XT - 1) / XT;
-  p.units = p.nxt * p.nbands * a.N;
+  p.units = p.nxt * p.nbands * p.nz;
   p.set = a.set;
   p.images = a.images;
   p.status = a.status;
@@ -1097,7 +1101,7 @@ cudaError_t launch_t(const ProjectArgs& a, cudaStream_t st) {
   const int64_t gmax = (int64_t)sms * per_sm;
   int64_t grid;
   if (p.nxt <= gmax) {  // tile-major ranges, nxt CTAs per (band, z) range
-    const int64_t W = p.nbands * a.N;
+    const int64_t W = p.nbands * p.nz;
     int64_t cpt = gmax / p.nxt;
     if (cpt > (W + 7) / 8) cpt = (W + 7) / 8;
     if (cpt < 1) cpt = 1;
