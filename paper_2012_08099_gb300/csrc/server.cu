@@ -118,6 +118,93 @@ class Arena {
   std::unordered_map<size_t, size_t> sizes_;
 };
 
+// Copies of submitted host volumes into pinned buffers, split over worker
+// threads: one thread's memcpy runs well below the host memory bandwidth,
+// and submit() must finish the copy before it returns.
+class CopyPool {
+ public:
+  explicit CopyPool(int workers) {
+    for (int i = 0; i < workers; ++i) threads_.emplace_back([this] { run(); });
+  }
+  ~CopyPool() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (std::thread& t : threads_) t.join();
+  }
+  // dst <- src (bytes); returns when the whole copy is done
+  void copy(void* dst, const void* src, size_t bytes) {
+    constexpr size_t kMinPart = 1u << 20;
+    size_t parts = bytes / kMinPart;
+    if (parts > threads_.size() + 1) parts = threads_.size() + 1;
+    if (parts <= 1) {
+      std::memcpy(dst, src, bytes);
+      return;
+    }
+    Done done;
+    done.left = (int)parts - 1;
+    const size_t step = ((bytes + parts - 1) / parts + 4095) & ~size_t(4095);
+    unsigned char* d = static_cast<unsigned char*>(dst);
+    const unsigned char* sp = static_cast<const unsigned char*>(src);
+    size_t first = step < bytes ? step : bytes;
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      int queued = 0;
+      for (size_t at = first; at < bytes; at += step) {
+        const size_t n = (bytes - at) < step ? (bytes - at) : step;
+        jobs_.push_back(Part{d + at, sp + at, n, &done});
+        ++queued;
+      }
+      done.left = queued;  // parts past the first, which this thread copies
+    }
+    cv_.notify_all();
+    std::memcpy(d, sp, first);
+    std::unique_lock<std::mutex> lk(done.mu);
+    done.cv.wait(lk, [&] { return done.left == 0; });
+  }
+
+ private:
+  struct Done {
+    std::mutex mu;
+    std::condition_variable cv;
+    int left = 0;
+  };
+  struct Part {
+    unsigned char* dst;
+    const unsigned char* src;
+    size_t n;
+    Done* done;
+  };
+  void run() {
+    for (;;) {
+      Part p;
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return stop_ || !jobs_.empty(); });
+        if (jobs_.empty()) return;  // stop requested and nothing left
+        p = jobs_.front();
+        jobs_.pop_front();
+      }
+      std::memcpy(p.dst, p.src, p.n);
+      std::lock_guard<std::mutex> lk(p.done->mu);
+      if (--p.done->left == 0) p.done->cv.notify_all();
+    }
+  }
+  std::vector<std::thread> threads_;
+  std::mutex mu_;
+  std::condition_variable cv_;
+  std::deque<Part> jobs_;
+  bool stop_ = false;
+};
+
+int copy_workers() {
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int n = hw > 2 ? (int)(hw / 2) : 1;
+  return n > 8 ? 8 : n;
+}
+
 // Pinned host buffers reused by size class (powers of two from 4 KiB).
 class PinnedPool {
  public:
@@ -209,6 +296,7 @@ struct dpma_server {
   int device = 0;
   Arena arena;
   PinnedPool pinned;
+  CopyPool copier{copy_workers()};
   std::vector<cudaStream_t> streams;
   int next_stream = 0;
   // one control block per in-flight slot (a group holds at least one request)
@@ -685,7 +773,7 @@ dpma_status dpma_server_submit_keyed(dpma_server* s, const dpma_volume_desc* des
     delete r;
     return sfail(DPMA_ERR_OOM, "pinned host memory");
   }
-  std::memcpy(r->h_in, d.volume, r->vbytes);  // the caller's buffer is free on return
+  s->copier.copy(r->h_in, d.volume, r->vbytes);  // the caller's buffer is free on return
   r->d = d;
   r->d.volume = r->h_in;
   std::lock_guard<std::mutex> lk(s->mu);
