@@ -138,8 +138,9 @@ std::vector<StageEvent> g_pending;
 std::vector<cudaEvent_t> g_free_events;
 double g_stage_ms[4] = {0, 0, 0, 0};
 int64_t g_stage_launches[4] = {0, 0, 0, 0};
-// kernel launches each stage makes (memsets are not kernels of this library)
-constexpr int kStageKernels[4] = {0, 1, 2, 1};
+// kernel launches each stage makes: clear, projection, image moments +
+// partial reduction, combine
+constexpr int kStageKernels[4] = {1, 1, 2, 1};
 
 cudaEvent_t take_event() {
   if (!g_free_events.empty()) {
@@ -201,10 +202,8 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
   if (e != cudaSuccess) return cuda_fail(e, "combine plan");
   StageRecorder rec(st);
   void* images = ws + w.off_img;
-  e = cudaMemsetAsync(images, 0, w.img_bytes, st);
+  e = launch_clear(images, w.img_bytes, reinterpret_cast<int*>(ws + w.off_status), st);
   if (e != cudaSuccess) return cuda_fail(e, "clear images");
-  e = cudaMemsetAsync(ws + w.off_status, 0, sizeof(int), st);
-  if (e != cudaSuccess) return cuda_fail(e, "clear status");
   rec.mark(0);
   ProjectArgs a{};
   a.vol = volume;

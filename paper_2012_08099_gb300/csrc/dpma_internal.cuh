@@ -76,6 +76,11 @@ struct ProjectArgs {
   int64_t z0 = 0, nz = 0;
 };
 
+// Zeroes `bytes` (a multiple of 4) at `p` and, if non-null, the status word,
+// in one launch: 16-byte stores when p is 16-byte aligned, 4-byte stores for
+// the tail.  Falls back to cudaMemsetAsync for a misaligned p.
+cudaError_t launch_clear(void* p, size_t bytes, int* status, cudaStream_t st);
+
 // Step 1: images must be zeroed by the caller (the launcher does not clear).
 cudaError_t launch_project(const ProjectArgs& a, cudaStream_t st);
 

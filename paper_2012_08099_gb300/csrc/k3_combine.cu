@@ -260,6 +260,36 @@ cudaError_t device_plan(int K, DevPlan* out) {
 
 }  // namespace
 
+namespace {
+__global__ void clear_kernel(uint32_t* p, int64_t n32, int* status) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (status && gid == 0) *status = 0;
+  const int64_t n16 = n32 >> 2;
+  uint4* q = reinterpret_cast<uint4*>(p);
+  for (int64_t i = gid; i < n16; i += stride) q[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int64_t i = (n16 << 2) + gid; i < n32; i += stride) p[i] = 0u;
+}
+}  // namespace
+
+cudaError_t launch_clear(void* p, size_t bytes, int* status, cudaStream_t st) {
+  if ((reinterpret_cast<uintptr_t>(p) & 15) != 0 || (bytes & 3) != 0) {
+    cudaError_t e = cudaMemsetAsync(p, 0, bytes, st);
+    if (e == cudaSuccess && status) e = cudaMemsetAsync(status, 0, sizeof(int), st);
+    return e;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t n32 = (int64_t)(bytes / 4);
+  int64_t blocks = (n32 / 4 + 255) / 256;
+  const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  clear_kernel<<<(unsigned)blocks, 256, 0, st>>>(static_cast<uint32_t*>(p), n32, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce_partials(const void* partials, const int64_t* blk_base, int P, int K,
                                    bool is_float, void* m2d, cudaStream_t st) {
   RedParams p{};

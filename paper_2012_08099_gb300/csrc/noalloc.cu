@@ -119,8 +119,7 @@ extern "C" dpma_status dpma_moments_noalloc(const void* volume, int64_t L, int64
   if (e != cudaSuccess) return fail_with(DPMA_ERR_CUDA, cudaGetErrorString(e));
 
   // the three steps; images and the status word must start at zero
-  e = cudaMemsetAsync(ws + off_img, 0, img_bytes, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ws + off_status, 0, sizeof(int), st);
+  e = launch_clear(ws + off_img, img_bytes, reinterpret_cast<int*>(ws + off_status), st);
   if (e != cudaSuccess) return fail_with(DPMA_ERR_CUDA, cudaGetErrorString(e));
   ProjectArgs a{};
   a.vol = volume;
