@@ -26,7 +26,9 @@
 // step: row sums across the half-warp (image 1), column sums through
 // shared slots (image 2), diagonal sums through shared buffers (7, 8).
 // After each step a barrier hands these per-step results to all 256 threads,
-// which merge them into the global images in an evenly divided task loop.
+// which merge them into the global images in an evenly divided task loop
+// (for float volumes during the next step, between its sums and its
+// in-slice reductions, so the merge's latencies overlap that work).
 //
 // Float volumes keep every sum compensated: each accumulator is a pair
 // (hi, lo) updated with the error-free TwoSum, so a pixel carries float-float
@@ -603,6 +605,10 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
     }
   };
 
+  constexpr bool kDeferMerge = FL;
+  bool pend = false;  // a step whose merge is still to do (float volumes)
+  int pend_sb = 0;
+  int64_t pend_z = 0;
   bool aborted = false;
   int64_t s = 0;   // CTA step counter
   int64_t u = ub;  // next unit
@@ -623,6 +629,53 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
     const int64_t F2 = set.F[2];
     set_roles(x0, y0);
     __syncthreads();
+    // merge of the step results in buffer msb (image 2 slots, exit buffer)
+    // for slice mz of this segment
+    auto merge_step = [&](int msb, int64_t mz) {
+      // (a) image 2, one quarter of a column's TY partials per thread
+      {
+        const A* e0 = slot2 + ((size_t)(msb * TY + part2 * (TY / 4)) * XT + col2) * PW;
+        A h = e0[0];
+        float l = 0.f;
+        if constexpr (FL) l = e0[1];
+#pragma unroll
+        for (int g = 1; g < TY / 4; ++g) {
+          const A* e = e0 + (size_t)g * XT * PW;
+          if constexpr (FL) pair_acc(h, l, e[0], e[1]);
+          else h += e[0];
+        }
+#pragma unroll
+        for (int m = 1; m <= 2; m <<= 1) {
+          if constexpr (FL) {
+            const float oh = __shfl_xor_sync(0xffffffffu, h, m), ol = __shfl_xor_sync(0xffffffffu, l, m);
+            pair_acc(h, l, oh, ol);
+          } else {
+            h += __shfl_xor_sync(0xffffffffu, h, m);
+          }
+        }
+        if (ok2) emit(img2 + mz * F2, h, l);
+      }
+      // (b) the exit buffer, one slot per task
+#pragma unroll
+      for (int i = 0; i < (NTASK + NT - 1) / NT; ++i) {
+        const int t = tid + i * NT;
+        if (t < NTASK) {
+          const int4 rd = roles[t];
+          A* c = xb + (size_t)msb * X::ES * PW + (size_t)t * PW;
+          const A hv = c[0];
+          float lv = 0.f;
+          if constexpr (FL) lv = c[1];
+          if (t >= X::E7) {  // diagonal cells accumulate: clear for the step after next
+            c[0] = (A)0;
+            if constexpr (FL) c[1] = 0.f;
+          }
+          if (mz >= rd.w) {
+            const int64_t base = (int64_t)(((uint64_t)(uint32_t)rd.y << 32) | (uint32_t)rd.x);
+            emit(img + (base + mz * (int64_t)rd.z), hv, lv);
+          }
+        }
+      }
+    };
     int64_t z = za;
     while (z < zb && !aborted) {
 #pragma unroll
@@ -700,6 +753,12 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
           }
       }
 
+      if constexpr (kDeferMerge) {  // the previous step's merge
+        if (pend) {
+          merge_step(pend_sb, pend_z);
+          pend = false;
+        }
+      }
       // ---- 3. images in the slice: column sums (2), row sums (1), diagonals (7, 8)
       {
         A* s2 = slot2 + ((size_t)(sb * TY + ty) * XT + xl) * PW;
@@ -949,55 +1008,25 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
         }
       }
 
-      // ---- 7. merge this step's complete results into the images
-      // (a) image 2, one quarter of a column's TY partials per thread
-      {
-        const A* e0 = slot2 + ((size_t)(sb * TY + part2 * (TY / 4)) * XT + col2) * PW;
-        A h = e0[0];
-        float l = 0.f;
-        if constexpr (FL) l = e0[1];
-#pragma unroll
-        for (int g = 1; g < TY / 4; ++g) {
-          const A* e = e0 + (size_t)g * XT * PW;
-          if constexpr (FL) pair_acc(h, l, e[0], e[1]);
-          else h += e[0];
-        }
-#pragma unroll
-        for (int m = 1; m <= 2; m <<= 1) {
-          if constexpr (FL) {
-            const float oh = __shfl_xor_sync(0xffffffffu, h, m), ol = __shfl_xor_sync(0xffffffffu, l, m);
-            pair_acc(h, l, oh, ol);
-          } else {
-            h += __shfl_xor_sync(0xffffffffu, h, m);
-          }
-        }
-        if (ok2) emit(img2 + z * F2, h, l);
+      // ---- 7. merge this step's complete results into the images: now for
+      // integer volumes; for float volumes during the next step (its buffers
+      // are not rewritten before the next step's barrier), where the merge's
+      // load and shuffle latencies overlap that step's sums (measured 6%)
+      if constexpr (kDeferMerge) {
+        pend = true;
+        pend_sb = sb;
+        pend_z = z;
+      } else {
+        merge_step(sb, z);
       }
-      // (b) the exit buffer, one slot per task
-#pragma unroll
-      for (int i = 0; i < (NTASK + NT - 1) / NT; ++i) {
-        const int t = tid + i * NT;
-        if (t < NTASK) {
-          const int4 rd = roles[t];
-          A* c = xc + (size_t)t * PW;
-          const A hv = c[0];
-          float lv = 0.f;
-          if constexpr (FL) lv = c[1];
-          if (t >= X::E7) {  // diagonal cells accumulate: clear for the step after next
-            c[0] = (A)0;
-            if constexpr (FL) c[1] = 0.f;
-          }
-          if (z >= rd.w) {
-            const int64_t base = (int64_t)(((uint64_t)(uint32_t)rd.y << 32) | (uint32_t)rd.x);
-            emit(img + (base + z * (int64_t)rd.z), hv, lv);
-          }
-        }
-      }
-
       ++s;
       ++u;
       ++z;
     }
+    }
+    if constexpr (kDeferMerge) {  // the segment's last step
+      if (pend && !aborted) merge_step(pend_sb, pend_z);
+      pend = false;
     }
     if (!aborted) {
       drain(x0, y0, zb - 1);
