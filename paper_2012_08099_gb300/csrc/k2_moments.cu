@@ -8,15 +8,14 @@
 // each image (its DRT listing); on a GPU the separable power sums above are
 // cheaper and exact, and they give identical results.
 //
-// One warp handles one image row: lanes stride over the row (four loads in
-// flight per lane) and accumulate F_b for b = 0..K, a butterfly reduction
-// gives every lane the row totals, and lane t then adds (s - off_s)^a F_b
-// for the (a, b) pairs it owns.  A CTA covers kRowsPerBlock = 8 rows of one
-// image, so a 512^3 volume's seven images give ~450 CTAs; each CTA writes
-// one partial vector and a small kernel sums the partials per image.
-// Integer images accumulate exactly in int128; float images (doubles) are
-// split into float32 pairs with integer operations and accumulate in
-// float-float, so no FP64 arithmetic happens here.
+// Integer images: one thread per row segment of kSegLen pixels runs
+// cascaded sums (additions only) and converts them exactly to the
+// segment's power sums F_b; the CTA then folds s^a F_b over its segments.
+// Float images (doubles): one warp per image row; lanes stride over the
+// row, split each double into a float32 pair with integer operations and
+// accumulate F_b in float-float (no FP64 arithmetic), a butterfly reduction
+// gives the row totals, and each lane adds s^a F_b for the pairs it owns.
+// Every CTA writes one partial vector; a small kernel sums them per image.
 #include <cstdint>
 
 #include "dpma_internal.cuh"
@@ -33,101 +32,166 @@ struct K2Params {
   ImageSet set;
   int K;
   int npairs;
+  int seg_len;  // integer images: pixels per row segment
   int64_t blk_base[kMaxImages + 1];  // first block of each image; [P] = total
   void* partials;                    // [block][npairs] int128 or float2
 };
 
-__device__ __forceinline__ i128 shfl_xor_i128(i128 v, int m) {
-  unsigned long long lo = (unsigned long long)(u128)v;
-  unsigned long long hi = (unsigned long long)((u128)v >> 64);
-  lo = __shfl_xor_sync(0xffffffffu, lo, m);
-  hi = __shfl_xor_sync(0xffffffffu, hi, m);
-  return (i128)(((u128)hi << 64) | lo);
+// Integer images by cascaded sums -------------------------------------------
+//
+// For a row segment of n pixels I_0 .. I_{n-1}, running A_0 += I_i,
+// A_1 += A_0, ..., A_K += A_{K-1} (each with the value just updated) leaves
+// A_j = sum_i C(n-1-i+j, j) I_i, which is sum_w w^(j)/j! I with w = n - i and
+// w^(j) the rising factorial.  Rising factorials expand in powers through the
+// Stirling numbers of the second kind, w^b = sum_j (-1)^(b-j) S(b,j) w^(j),
+// so Q_b = sum_w w^b I = sum_j (-1)^(b-j) S(b,j) j! A_j.  The signed image
+// coordinate is c = f - off_f = D - w with D = f_start + n - off_f, and the
+// row power sums F_b = sum (D - w)^b I follow from the Q_k by a binomial
+// shift.  Every step is a ring operation, so all of it is exact modulo
+// 2^128, and the 2-D moments, which fit in int128, come out exact.  Per pixel
+// this costs K + 1 additions instead of K products.
+constexpr int kSegLenMax = 128;    // pixels per segment at most: A_0 .. A_4 fit in 64 bits
+constexpr int kUnitThreads = 128;  // segments per CTA
+
+struct StirlingTable {
+  int64_t v[kMaxK + 1][kMaxK + 1];  // (-1)^(b-j) S(b,j) j!
+};
+constexpr StirlingTable make_stirling() {
+  StirlingTable t{};
+  int64_t S[kMaxK + 1][kMaxK + 1] = {};
+  S[0][0] = 1;
+  for (int b = 1; b <= kMaxK; ++b)
+    for (int j = 1; j <= b; ++j) S[b][j] = j * S[b - 1][j] + S[b - 1][j - 1];
+  for (int b = 0; b <= kMaxK; ++b) {
+    int64_t fact = 1;
+    for (int j = 0; j <= b; ++j) {
+      if (j > 0) fact *= j;
+      t.v[b][j] = ((b - j) & 1 ? -1 : 1) * S[b][j] * fact;
+    }
+  }
+  return t;
 }
+__constant__ StirlingTable c_stirling = make_stirling();
 
 template <int K>
-__global__ void __launch_bounds__(kThreads) k2_int_kernel(K2Params p) {
+__global__ void __launch_bounds__(kUnitThreads) k2_int_cascade_kernel(K2Params p) {
+  constexpr int NB = K + 1;
+  constexpr int CH = kUnitThreads / NB;  // unit chunks per power b in the fold
   const int blk = blockIdx.x;
   int k = 0;
   while (k + 1 < p.set.P && blk >= p.blk_base[k + 1]) ++k;
   const int64_t chunk = blk - p.blk_base[k];
   const int64_t S = p.set.S[k], F = p.set.F[k];
   const int64_t off_s = p.set.off_s[k], off_f = p.set.off_f[k];
+  const int64_t seg = p.seg_len;
+  const int64_t nseg = (F + seg - 1) / seg;
   const uint32_t* img = static_cast<const uint32_t*>(p.images) + p.set.base[k];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = threadIdx.x;
 
-  // pairs owned by this lane: index lane and lane + 32
-  int pa[2], pb[2];
-  for (int t = 0; t < 2; ++t) {
-    int idx = lane + 32 * t;
-    pa[t] = -1; pb[t] = -1;
-    if (idx < p.npairs) {
-      int n = 0;
-      while ((n + 1) * (n + 2) / 2 <= idx) ++n;
-      int a = n - (idx - n * (n + 1) / 2);
-      pa[t] = a; pb[t] = n - a;
-    }
-  }
-  i128 T[2] = {0, 0};
+  __shared__ u128 Fs[kUnitThreads][NB];  // row power sums of each segment
+  __shared__ int64_t Cs[kUnitThreads];   // its signed row coordinate
+  __shared__ u128 part[NB][CH][NB];      // fold partials [b][chunk][a]
 
-  const int64_t r0 = chunk * kRowsPerBlock;
-  const int64_t r1 = (r0 + kRowsPerBlock < S) ? r0 + kRowsPerBlock : S;
-  for (int64_t s = r0 + warp; s < r1; s += kWarps) {
-    i128 Fb[K + 1];
+  // 1. one segment per thread
+  const int64_t u = chunk * kUnitThreads + t;
+  u128 Fb[NB];
 #pragma unroll
-    for (int b = 0; b <= K; ++b) Fb[b] = 0;
-    const uint32_t* row = img + s * F;
-    for (int64_t f0 = lane; f0 < F; f0 += 4 * 32) {
-      uint32_t vv[4];
+  for (int b = 0; b < NB; ++b) Fb[b] = 0;
+  int64_t cs = 0;
+  if (u < S * nseg) {
+    const int64_t s = u / nseg, g = u - s * nseg;
+    const int64_t fs = g * seg;
+    const int n = (int)(F - fs < seg ? F - fs : seg);
+    const uint32_t* row = img + s * F + fs;
+    constexpr int N64 = NB < 5 ? NB : 5;  // A_0 .. A_4 in 64 bits
+    uint64_t a64[N64];
+    u128 a128[NB > 5 ? NB - 5 : 1];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int64_t f = f0 + q * 32;
-        vv[q] = f < F ? __ldg(row + f) : 0u;
+    for (int j = 0; j < N64; ++j) a64[j] = 0;
+#pragma unroll
+    for (int j = 0; j < (NB > 5 ? NB - 5 : 1); ++j) a128[j] = 0;
+    for (int i = 0; i < n; ++i) {
+      a64[0] += __ldg(row + i);
+#pragma unroll
+      for (int j = 1; j < N64; ++j) a64[j] += a64[j - 1];
+      if constexpr (NB > 5) {
+        a128[0] += a64[4];
+#pragma unroll
+        for (int j = 1; j < NB - 5; ++j) a128[j] += a128[j - 1];
       }
+    }
+    u128 A[NB];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (!vv[q]) continue;
-        const int64_t c = f0 + q * 32 - off_f;
-        i128 t = (i128)vv[q];
+    for (int j = 0; j < NB; ++j) A[j] = j < 5 ? (u128)a64[j < 5 ? j : 0] : a128[j >= 5 ? j - 5 : 0];
+    // Q_b = sum_j (-1)^(b-j) S(b,j) j! A_j, then the shift to c = D - w:
+    // with m_k = (-1)^k Q_k, F_b = sum_k C(b,k) D^(b-k) m_k, built by the
+    // Pascal recurrence m_b += D m_(b-1) applied K times
 #pragma unroll
-        for (int b = 0; b <= K; ++b) {
-          Fb[b] += t;
-          if (b < K) t *= (i128)c;
+    for (int b = 0; b < NB; ++b) {
+      u128 q = 0;
+#pragma unroll
+      for (int j = 0; j <= b; ++j) q += (u128)(i128)c_stirling.v[b][j] * A[j];
+      Fb[b] = (b & 1) ? (u128)0 - q : q;
+    }
+    const u128 D = (u128)(i128)(fs + n - off_f);
+#pragma unroll
+    for (int i = 1; i < NB; ++i)
+#pragma unroll
+      for (int b = NB - 1; b >= i; --b) Fb[b] += D * Fb[b - 1];
+    cs = s - off_s;
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b) Fs[t][b] = Fb[b];
+  Cs[t] = cs;
+  __syncthreads();
+
+  // 2. fold: thread (b, chunk c) takes a contiguous range of the CTA's
+  // segments, sums the segments of each row, and adds s^a F_b(row) for
+  // a <= K - b
+  if (t < NB * CH) {
+    const int b = t / CH, c = t - b * CH;
+    constexpr int per = (kUnitThreads + CH - 1) / CH;
+    const int u0 = c * per, u1 = (u0 + per < kUnitThreads) ? u0 + per : kUnitThreads;
+    u128 T[NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a) T[a] = 0;
+    auto fold = [&](u128 pw, int64_t srow) {
+      const u128 sv = (u128)(i128)srow;
+      T[0] += pw;
+#pragma unroll
+      for (int a = 1; a < NB; ++a) {
+        if (a > K - b) break;
+        pw *= sv;
+        T[a] += pw;
+      }
+    };
+    if (u0 < u1) {
+      u128 cur = Fs[u0][b];
+      int64_t cur_s = Cs[u0];
+      for (int uu = u0 + 1; uu < u1; ++uu) {
+        if (Cs[uu] == cur_s) {
+          cur += Fs[uu][b];
+        } else {
+          fold(cur, cur_s);
+          cur = Fs[uu][b];
+          cur_s = Cs[uu];
         }
       }
+      fold(cur, cur_s);
     }
 #pragma unroll
-    for (int b = 0; b <= K; ++b) {
-#pragma unroll
-      for (int m = 16; m >= 1; m >>= 1) Fb[b] += shfl_xor_i128(Fb[b], m);
-    }
-    const i128 cs = (i128)(s - off_s);
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      if (pa[t] < 0) continue;
-      i128 w = 1;
-      for (int e = 0; e < pa[t]; ++e) w *= cs;
-      i128 fb = 0;
-#pragma unroll
-      for (int b = 0; b <= K; ++b)
-        if (b == pb[t]) fb = Fb[b];
-      T[t] += w * fb;
-    }
+    for (int a = 0; a < NB; ++a) part[b][c][a] = T[a];
   }
-
-  // reduce the kWarps partial vectors of this CTA
-  __shared__ i128 red[kWarps][64];
-  red[warp][lane] = T[0];
-  red[warp][lane + 32] = T[1];
   __syncthreads();
-  if (warp == 0) {
-    for (int t = 0; t < 2; ++t) {
-      const int idx = lane + 32 * t;
-      if (idx >= p.npairs) continue;
-      i128 acc = 0;
-      for (int w = 0; w < kWarps; ++w) acc += red[w][idx];
-      static_cast<i128*>(p.partials)[(int64_t)blk * p.npairs + idx] = acc;
-    }
+
+  // 3. pair (a, b), number n (n + 1) / 2 + b with n = a + b, sums the chunks
+  for (int j = t; j < p.npairs; j += kUnitThreads) {
+    int n = 0;
+    while ((n + 1) * (n + 2) / 2 <= j) ++n;
+    const int b = j - n * (n + 1) / 2, a = n - b;
+    u128 acc = 0;
+    for (int c = 0; c < CH; ++c) acc += part[b][c][a];
+    static_cast<i128*>(p.partials)[(int64_t)blk * p.npairs + j] = (i128)acc;
   }
 }
 
@@ -258,11 +322,29 @@ __global__ void __launch_bounds__(kThreads) k2_f32_kernel(K2Params p) {
   }
 }
 
-int64_t blocks_of(const ImageSet& set, int64_t* base) {
+// Pixels per row segment of integer images: 16 .. 128, the largest power of
+// two that still gives about 78 K segments (16 warps per SM) over all images.
+int int_seg_len(const ImageSet& set) {
+  int64_t pixels = 0;
+  for (int k = 0; k < set.P; ++k) pixels += set.S[k] * set.F[k];
+  int seg = kSegLenMax;
+  while (seg > 16 && pixels / seg < 152 * 16 * 32) seg >>= 1;
+  return seg;
+}
+
+// CTAs of step 2 per image: float images take kRowsPerBlock rows per CTA,
+// integer images kUnitThreads row segments per CTA.
+int64_t blocks_of(const ImageSet& set, bool is_float, int64_t* base) {
   int64_t at = 0;
   for (int k = 0; k < set.P; ++k) {
     if (base) base[k] = at;
-    at += (set.S[k] + kRowsPerBlock - 1) / kRowsPerBlock;
+    if (is_float) {
+      at += (set.S[k] + kRowsPerBlock - 1) / kRowsPerBlock;
+    } else {
+      const int64_t seg = int_seg_len(set);
+      const int64_t units = set.S[k] * ((set.F[k] + seg - 1) / seg);
+      at += (units + kUnitThreads - 1) / kUnitThreads;
+    }
   }
   if (base) base[set.P] = at;
   return at;
@@ -271,7 +353,8 @@ int64_t blocks_of(const ImageSet& set, int64_t* base) {
 }  // namespace
 
 size_t moments2d_partials_bytes(const ImageSet& set, int K, bool is_float) {
-  return (size_t)blocks_of(set, nullptr) * num_2d(K) * (is_float ? sizeof(float2) : sizeof(i128));
+  return (size_t)blocks_of(set, is_float, nullptr) * num_2d(K) *
+         (is_float ? sizeof(float2) : sizeof(i128));
 }
 
 // defined in k3_combine.cu: sums the block partials into per-image moments
@@ -285,13 +368,14 @@ cudaError_t launch_image_moments(const void* images, const ImageSet& set, int K,
   p.set = set;
   p.K = K;
   p.npairs = num_2d(K);
-  const int64_t nblk = blocks_of(set, p.blk_base);
+  p.seg_len = int_seg_len(set);
+  const int64_t nblk = blocks_of(set, is_float, p.blk_base);
   p.partials = partials;
   switch (K) {
 #define DPMA_K2_CASE(k)                                                   \
   case k:                                                                 \
     if (is_float) k2_f32_kernel<k><<<(unsigned)nblk, kThreads, 0, st>>>(p); \
-    else k2_int_kernel<k><<<(unsigned)nblk, kThreads, 0, st>>>(p);          \
+    else k2_int_cascade_kernel<k><<<(unsigned)nblk, kUnitThreads, 0, st>>>(p); \
     break;
     DPMA_K2_CASE(0) DPMA_K2_CASE(1) DPMA_K2_CASE(2) DPMA_K2_CASE(3) DPMA_K2_CASE(4)
     DPMA_K2_CASE(5) DPMA_K2_CASE(6) DPMA_K2_CASE(7) DPMA_K2_CASE(8)
