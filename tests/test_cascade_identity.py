@@ -1,0 +1,80 @@
+"""The identity behind the integer image-moment kernel, in exact integers.
+
+Running A_0 += I_i, A_1 += A_0, ..., A_K += A_(K-1) over a row segment of n
+pixels gives A_j = sum_i C(n-1-i+j, j) I_i.  With w = n - i, the power sums
+sum_w w^b I are sum_j (-1)^(b-j) S(b,j) j! A_j (S: Stirling numbers of the
+second kind), and the Pascal recurrence m_b += D m_(b-1), applied K times
+to m_k = (-1)^k Q_k, yields sum (D - w)^b I, the power sums in the signed
+coordinate c = f - off_f with D = f_start + n - off_f (Eq. 1 with the
+origin shift of Sec. 5).  The kernel does all of it modulo 2^128; the test
+does the same and compares with the direct sums, and checks that A_0..A_4
+stay below 2^64 for segments of at most 128 pixels of 32-bit values.
+"""
+import random
+from math import comb, factorial
+
+M128 = 1 << 128
+
+
+def stirling2(n, k):
+    table = [[0] * (n + 1) for _ in range(n + 1)]
+    table[0][0] = 1
+    for i in range(1, n + 1):
+        for j in range(1, i + 1):
+            table[i][j] = j * table[i - 1][j] + table[i - 1][j - 1]
+    return table[n][k]
+
+
+def segment_power_sums(I, K, f_start, off_f):
+    """The kernel's steps for one segment, modulo 2^128."""
+    A = [0] * (K + 1)
+    for v in I:
+        A[0] = (A[0] + v) % M128
+        for j in range(1, K + 1):
+            A[j] = (A[j] + A[j - 1]) % M128
+    m = []
+    for b in range(K + 1):
+        q = sum((-1) ** (b - j) * stirling2(b, j) * factorial(j) * A[j] for j in range(b + 1))
+        m.append((-q if b & 1 else q) % M128)
+    D = f_start + len(I) - off_f
+    for i in range(1, K + 1):
+        for b in range(K, i - 1, -1):
+            m[b] = (m[b] + D * m[b - 1]) % M128
+    return A, m
+
+
+def test_cascade_matches_direct_power_sums():
+    rng = random.Random(11)
+    for _ in range(200):
+        K = rng.randint(0, 8)
+        n = rng.randint(1, 128)
+        f_start = rng.randint(0, 4000)
+        off_f = rng.randint(0, 4000)
+        I = [rng.choice([0, rng.randint(0, 2**32 - 1)]) for _ in range(n)]
+        A, F = segment_power_sums(I, K, f_start, off_f)
+        for b in range(K + 1):
+            direct = sum((f_start + i - off_f) ** b * v for i, v in enumerate(I))
+            assert F[b] == direct % M128, (K, n, b)
+        for j in range(K + 1):
+            assert A[j] == sum(comb(n - 1 - i + j, j) * v for i, v in enumerate(I)) % M128
+
+
+def test_low_cascade_sums_fit_64_bits():
+    # worst case: 128 pixels, every pixel 2^32 - 1
+    top = 2**32 - 1
+    for j in range(5):
+        assert top * comb(128 + j, j + 1) < 2**64
+    assert top * comb(128 + 5, 6) >= 2**64  # A_5 needs the 128-bit path
+
+
+def test_summed_segments_give_the_row():
+    """Segments of one row add up to the row's power sums (the CTA sums them)."""
+    rng = random.Random(5)
+    K, F, off_f, seg = 6, 300, 150, 32
+    row = [rng.randint(0, 10**6) for _ in range(F)]
+    tot = [0] * (K + 1)
+    for fs in range(0, F, seg):
+        _, Fs = segment_power_sums(row[fs:fs + seg], K, fs, off_f)
+        tot = [(a + b) % M128 for a, b in zip(tot, Fs)]
+    for b in range(K + 1):
+        assert tot[b] == sum((f - off_f) ** b * v for f, v in enumerate(row)) % M128
