@@ -605,7 +605,9 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
     }
   };
 
-  constexpr bool kDeferMerge = FL;
+  // deferred merges pay off with two CTAs per SM (float volumes with six or
+  // more images); with one CTA of 4 x 4 micro-tiles they measured slower
+  constexpr bool kDeferMerge = FL && BYT == 2;
   bool pend = false;  // a step whose merge is still to do (float volumes)
   int pend_sb = 0;
   int64_t pend_z = 0;
@@ -1008,10 +1010,11 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
         }
       }
 
-      // ---- 7. merge this step's complete results into the images: now for
-      // integer volumes; for float volumes during the next step (its buffers
-      // are not rewritten before the next step's barrier), where the merge's
-      // load and shuffle latencies overlap that step's sums (measured 6%)
+      // ---- 7. merge this step's complete results into the images: now, or
+      // for float volumes with six or more images during the next step (its
+      // buffers are not rewritten before the next step's barrier), where the
+      // merge's load and shuffle latencies overlap that step's sums
+      // (measured 6%)
       if constexpr (kDeferMerge) {
         pend = true;
         pend_sb = sb;
