@@ -94,7 +94,15 @@ struct DeviceState {
   void* host_out = nullptr;
   cudaStream_t copy_stream = nullptr;  // host-to-device chunks of dpma_moments_host
   cudaEvent_t chunk_ready = nullptr;
+  int* h_status = nullptr;  // pinned: the synchronous calls read the status word here
 };
+
+// The pinned host word that receives the device status (a pageable
+// destination would make every synchronous call pay a staged copy).
+cudaError_t ensure_host_status(DeviceState* s) {
+  if (s->h_status) return cudaSuccess;
+  return cudaMallocHost(reinterpret_cast<void**>(&s->h_status), sizeof(int));
+}
 
 std::mutex g_states_mu;
 std::unordered_map<int, DeviceState*> g_states;
@@ -357,12 +365,15 @@ dpma_status dpma_moments(const void* volume, int64_t L, int64_t M, int64_t N, dp
   e = ensure_buffer(&ds->ws, &ds->ws_bytes, w.total);
   if (e != cudaSuccess) return cuda_fail(e, "workspace");
   unsigned char* ws = static_cast<unsigned char*>(ds->ws);
+  e = ensure_host_status(ds);
+  if (e != cudaSuccess) return cuda_fail(e, "pinned status word");
   s = enqueue(volume, L, M, N, dtype, K, out, ds->stream, ws, w);
   if (s != DPMA_OK) return s;
-  int status = 0;
-  e = cudaMemcpyAsync(&status, ws + w.off_status, sizeof(int), cudaMemcpyDeviceToHost, ds->stream);
+  e = cudaMemcpyAsync(ds->h_status, ws + w.off_status, sizeof(int), cudaMemcpyDeviceToHost,
+                      ds->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ds->stream);
   if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+  const int status = *ds->h_status;
   if (status == DPMA_ERR_TIMEOUT) return fail(DPMA_ERR_TIMEOUT, "a bounded device wait gave up");
   if (status) return fail(DPMA_ERR_INTERNAL, "combine division left a remainder");
   return DPMA_OK;
@@ -401,12 +412,15 @@ dpma_status dpma_moments_host(const void* host_volume, int64_t L, int64_t M, int
               ds->copy_stream, ds->chunk_ready);
   if (s != DPMA_OK) return s;
   const size_t out_bytes = (size_t)num_moments(K) * (is_float(dtype) ? 8 : 16);
-  int status = 0;
+  e = ensure_host_status(ds);
+  if (e != cudaSuccess) return cuda_fail(e, "pinned status word");
   e = cudaMemcpyAsync(host_out, ds->host_out, out_bytes, cudaMemcpyDeviceToHost, ds->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&status, ws + w.off_status, sizeof(int), cudaMemcpyDeviceToHost, ds->stream);
+    e = cudaMemcpyAsync(ds->h_status, ws + w.off_status, sizeof(int), cudaMemcpyDeviceToHost,
+                        ds->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ds->stream);
   if (e != cudaSuccess) return cuda_fail(e, "copy moments to host");
+  const int status = *ds->h_status;
   if (status == DPMA_ERR_TIMEOUT) return fail(DPMA_ERR_TIMEOUT, "a bounded device wait gave up");
   if (status) return fail(DPMA_ERR_INTERNAL, "combine division left a remainder");
   return DPMA_OK;
