@@ -114,12 +114,35 @@ __host__ __device__ __forceinline__ int stage_slices(int64_t slice_bytes, int N)
   return (int)(g < 1 ? 1 : (g < N ? g : N));
 }
 
+// Starts the copy of the stage of volume t that begins at slice z0 into the
+// stage buffer dst (cp.async, 16-byte blocks, one commit group); returns the
+// byte offset of slice z0 in the buffer.
+template <int NT>
+__device__ __forceinline__ int fetch_stage(const BTask& t, int z0, uint32_t* dst) {
+  const int esize = t.dtype == DPMA_U8 ? 1 : 2;
+  const int slice_bytes = t.L * t.M * esize;
+  const int G = stage_slices(slice_bytes, t.N);
+  const uintptr_t a = reinterpret_cast<uintptr_t>(t.vol) + (uintptr_t)z0 * slice_bytes;
+  const uintptr_t a16 = a & ~(uintptr_t)15;
+  const int hd = (int)(a - a16);
+  const int nb = (hd + min(G, t.N - z0) * slice_bytes + 15) >> 4;
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  for (int i = threadIdx.x; i < nb; i += NT)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d + 16 * i),
+                 "l"(a16 + 16 * (uintptr_t)i)
+                 : "memory");
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  return hd;
+}
+
 // Every image of one volume into shared memory (Eq. 4 for the image table of
-// dpma.h).  The volume streams through two shared buffers in stages of G
-// whole z-slices (as many as fit in one buffer): the 16-byte aligned blocks
+// dpma.h).  The volume streams through shared buffers in stages of G whole
+// z-slices (as many as fit in one buffer): the 16-byte aligned blocks
 // covering the next stage are copied with cp.async while the current stage
 // is processed (a 16-byte block holding a byte of the volume lies in the same
-// mapped page).  A position is a chunk of four consecutive voxels of one row,
+// mapped page).  Stage 0 arrives in `first` (copied ahead, during the
+// previous volume's moment stage, and complete on entry: it is slab buffer
+// 1); stage s uses slab buffer (s + 1) & 1.  A position is a chunk of four consecutive voxels of one row,
 // (y, c) with x0 = 4c; the stage's slices are split into Zg blocks so that
 // positions x blocks fill the CTA, and a thread walks its position through
 // the z of its block.  Four consecutive voxels of a row land on four
@@ -128,38 +151,24 @@ __host__ __device__ __forceinline__ int stage_slices(int64_t slice_bytes, int N)
 // registers over the block.  Every shared update is an atomic add; image k's
 // pixel index moves by a constant per z-step.
 template <typename T, bool WIDE, bool MANY, int NT>
-__device__ __forceinline__ void project_volume(const BTask& t, uint32_t* sm, uint32_t* slab) {
+__device__ __forceinline__ void project_volume(const BTask& t, uint32_t* sm, uint32_t* slab,
+                                               const uint32_t* first, int head0) {
   const int L = t.L, M = t.M, N = t.N, P = t.P;
   const int F3 = L + N - 1, F7 = L + M - 1;
   const int* o = t.img_off;
   const int slice_bytes = L * M * (int)sizeof(T);
   const int G = stage_slices(slice_bytes, N);
-  const uintptr_t vbase = reinterpret_cast<uintptr_t>(t.vol);
-  // starts the copy of the stage from slice z0 into buffer buf; returns the
-  // byte offset of slice z0 in the buffer
-  auto fetch = [&](int z0, int buf) -> int {
-    const uintptr_t a = vbase + (uintptr_t)z0 * slice_bytes;
-    const uintptr_t a16 = a & ~(uintptr_t)15;
-    const int hd = (int)(a - a16);
-    const int nb = (hd + min(G, N - z0) * slice_bytes + 15) >> 4;
-    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(slab + buf * kSlabWords);
-    for (int i = threadIdx.x; i < nb; i += NT)
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16 * i),
-                   "l"(a16 + 16 * (uintptr_t)i)
-                   : "memory");
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    return hd;
-  };
   const int nc = (L + 3) >> 2, npos = M * nc;
   const int Zg = t.zblocks[NT == 512 ? 1 : 0];  // z-blocks per stage
-  int head = fetch(0, 0), head_next = 0;
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-  __syncthreads();
-  for (int z0 = 0, buf = 0; z0 < N; z0 += G, buf ^= 1) {
-    // in flight while this stage is processed: the other buffer was last
-    // read in the previous stage, which ended with a barrier
-    if (z0 + G < N) head_next = fetch(z0 + G, buf ^ 1);
-    const unsigned char* S = reinterpret_cast<const unsigned char*>(slab + buf * kSlabWords);
+  int head = head0, head_next = 0;
+  const uint32_t* cur = first;
+  for (int z0 = 0, si = 0; z0 < N; z0 += G, ++si) {
+    // in flight while this stage is processed: buffer si & 1 was last read
+    // in stage si - 1 (or by the previous volume's moment stage), before a
+    // barrier
+    uint32_t* nxt = slab + (si & 1) * kSlabWords;
+    if (z0 + G < N) head_next = fetch_stage<NT>(t, z0 + G, nxt);
+    const unsigned char* S = reinterpret_cast<const unsigned char*>(cur);
     const int gz = min(G, N - z0), zlen = (gz + Zg - 1) / Zg;
     for (int it = threadIdx.x; it < npos * Zg; it += NT) {
       const int zg = it / npos, pos = it - zg * npos;
@@ -227,6 +236,7 @@ __device__ __forceinline__ void project_volume(const BTask& t, uint32_t* sm, uin
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     head = head_next;
+    cur = nxt;
     __syncthreads();
   }
 }
@@ -289,7 +299,7 @@ __device__ __forceinline__ void volume_moments(const BTask& t, const uint32_t* s
   const int K = t.K, P = t.P;
   const int npairs = (K + 1) * (K + 2) / 2;
   const int stride = K + 1;  // RT words per unit
-  constexpr int kScratch = 2 * kSlabWords * 4;
+  constexpr int kScratch = kSlabWords * 4;  // stage buffer 0 (buffer 1 takes a prefetch)
   const int U = min(NT, (int)(kScratch / (stride * (int)sizeof(RT) + 4)));
   RT* Rs = static_cast<RT*>(scratch);
   int* Ss = reinterpret_cast<int*>(Rs + (size_t)U * stride);
@@ -383,9 +393,10 @@ __device__ __forceinline__ void volume_moments(const BTask& t, const uint32_t* s
 }
 
 template <typename T, bool WIDE, int NT>
-__device__ __forceinline__ void project_any(const BTask& t, uint32_t* sm, uint32_t* slab) {
-  if (t.P > 5) project_volume<T, WIDE, true, NT>(t, sm, slab);
-  else project_volume<T, WIDE, false, NT>(t, sm, slab);
+__device__ __forceinline__ void project_any(const BTask& t, uint32_t* sm, uint32_t* slab,
+                                            const uint32_t* first, int head0) {
+  if (t.P > 5) project_volume<T, WIDE, true, NT>(t, sm, slab, first, head0);
+  else project_volume<T, WIDE, false, NT>(t, sm, slab, first, head0);
 }
 
 template <bool WIDE, int NT>
@@ -402,27 +413,39 @@ __global__ void __launch_bounds__(NT, 1) batch_fused_kernel(FusedParams p) {
   i128* Tacc = reinterpret_cast<i128*>(smem_raw);
   __shared__ ImgMeta meta[kMaxImages + 1];
   uint32_t* slab = reinterpret_cast<uint32_t*>(smem_raw + kPartBytes);  // [2][kSlabWords]
-  uint32_t* sm = slab + 2 * kSlabWords;                                  // images
-  __shared__ int s_task;
-  for (;;) {
-    if (threadIdx.x == 0) s_task = atomicAdd(p.counter, 1);
-    __syncthreads();
-    const int ti = s_task;
-    if (ti >= p.ntasks) break;
+  // stage buffer 1 receives the next volume's stage 0 while the moment
+  // stage uses buffer 0 as its scratch area
+  uint32_t* pre = slab + kSlabWords;
+  uint32_t* sm = slab + 2 * kSlabWords;  // images
+  __shared__ int s_first, s_next;
+  if (threadIdx.x == 0) s_first = atomicAdd(p.counter, 1);
+  __syncthreads();
+  int ti = s_first;  // s_first is never written again
+  int head_pre = ti < p.ntasks ? fetch_stage<NT>(p.tasks[p.order[ti]], 0, pre) : 0;
+  while (ti < p.ntasks) {
     const BTask t = p.tasks[p.order[ti]];
+    // the next volume is claimed now and its first stage is copied during
+    // this volume's moment stage, so neither latency is exposed
+    // (s_next was last read before the previous volume's final barrier)
+    if (threadIdx.x == 0) s_next = atomicAdd(p.counter, 1);
     for (int w = threadIdx.x; w < t.words + kSlackWords; w += NT) sm[w] = 0;
-    __syncthreads();
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();  // images zeroed, stage 0 in `pre`, s_next visible
+    const int next = s_next;
     i128* Tout = p.T + t.t_off;
     if (t.dtype == DPMA_U8) {
-      if (t.wide) project_any<uint8_t, true, NT>(t, sm, slab);
-      else project_any<uint8_t, false, NT>(t, sm, slab);
+      if (t.wide) project_any<uint8_t, true, NT>(t, sm, slab, pre, head_pre);
+      else project_any<uint8_t, false, NT>(t, sm, slab, pre, head_pre);
     } else {
-      if (t.wide) project_any<uint16_t, true, NT>(t, sm, slab);
-      else project_any<uint16_t, false, NT>(t, sm, slab);
+      if (t.wide) project_any<uint16_t, true, NT>(t, sm, slab, pre, head_pre);
+      else project_any<uint16_t, false, NT>(t, sm, slab, pre, head_pre);
     }
+    // the projection ended with a barrier: `pre` is free
+    if (next < p.ntasks) head_pre = fetch_stage<NT>(p.tasks[p.order[next]], 0, pre);
     if (t.wide) moments_any<true, NT>(t, sm, slab, Tacc, meta, Tout);
     else moments_any<false, NT>(t, sm, slab, Tacc, meta, Tout);
-    __syncthreads();  // s_task, the images and the scratch area are rewritten next
+    __syncthreads();  // s_next, the images and the scratch area are rewritten next
+    ti = next;
   }
 }
 
