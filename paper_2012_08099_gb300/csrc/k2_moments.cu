@@ -11,10 +11,9 @@
 // Integer images: one thread per row segment of kSegLen pixels runs
 // cascaded sums (additions only) and converts them exactly to the
 // segment's power sums F_b; the CTA then folds s^a F_b over its segments.
-// Float images (doubles): one warp per image row; lanes stride over the
-// row, split each double into a float32 pair with integer operations and
-// accumulate F_b in float-float (no FP64 arithmetic), a butterfly reduction
-// gives the row totals, and each lane adds s^a F_b for the pairs it owns.
+// Float images (doubles): the same segments; each double is split into a
+// float32 pair with integer operations and F_b accumulates in float-float
+// (no FP64 arithmetic), then the same fold in float-float.
 // Every CTA writes one partial vector; a small kernel sums them per image.
 #include <cstdint>
 
@@ -23,9 +22,6 @@
 namespace dpma {
 namespace {
 
-constexpr int kWarps = 8;
-constexpr int kThreads = kWarps * 32;
-constexpr int kRowsPerBlock = kWarps;  // one image row per warp
 
 struct K2Params {
   const void* images;
@@ -234,95 +230,110 @@ __device__ __forceinline__ void ff_mul_f(float hi, float lo, float c, float& rh,
   rl = __fsub_rn(e, __fsub_rn(rh, p));
 }
 
+// Float images: one thread per row segment (the layout of the integer
+// kernel).  The double pixels are split into float pairs with integer
+// operations; F_b of the segment accumulates in float-float (the power
+// chain I c^b by the FMA-based TwoProd); the CTA sums the segments of each
+// row in float-float and folds s^a F_b.
 template <int K>
-__global__ void __launch_bounds__(kThreads) k2_f32_kernel(K2Params p) {
+__global__ void __launch_bounds__(kUnitThreads) k2_f32_seg_kernel(K2Params p) {
+  constexpr int NB = K + 1;
+  constexpr int CH = kUnitThreads / NB;
   const int blk = blockIdx.x;
   int k = 0;
   while (k + 1 < p.set.P && blk >= p.blk_base[k + 1]) ++k;
   const int64_t chunk = blk - p.blk_base[k];
   const int64_t S = p.set.S[k], F = p.set.F[k];
   const int64_t off_s = p.set.off_s[k], off_f = p.set.off_f[k];
-  const unsigned long long* plane = static_cast<const unsigned long long*>(p.images) + p.set.base[k];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t seg = p.seg_len;
+  const int64_t nseg = (F + seg - 1) / seg;
+  const unsigned long long* img = static_cast<const unsigned long long*>(p.images) + p.set.base[k];
+  const int t = threadIdx.x;
 
-  int pa[2], pb[2];
-  for (int t = 0; t < 2; ++t) {
-    int idx = lane + 32 * t;
-    pa[t] = -1; pb[t] = -1;
-    if (idx < p.npairs) {
-      int n = 0;
-      while ((n + 1) * (n + 2) / 2 <= idx) ++n;
-      int a = n - (idx - n * (n + 1) / 2);
-      pa[t] = a; pb[t] = n - a;
-    }
-  }
-  float Th[2] = {0.f, 0.f}, Tl[2] = {0.f, 0.f};
+  __shared__ float2 Fs[kUnitThreads][NB];
+  __shared__ int64_t Cs[kUnitThreads];
+  __shared__ float2 part[NB][CH][NB];
 
-  const int64_t r0 = chunk * kRowsPerBlock;
-  const int64_t r1 = (r0 + kRowsPerBlock < S) ? r0 + kRowsPerBlock : S;
-  for (int64_t s = r0 + warp; s < r1; s += kWarps) {
-    float Fh[K + 1], Fl[K + 1];
+  // 1. one segment per thread
+  float Fh[NB], Fl[NB];
 #pragma unroll
-    for (int b = 0; b <= K; ++b) { Fh[b] = 0.f; Fl[b] = 0.f; }
-    const unsigned long long* row = plane + s * F;
-    for (int64_t f0 = lane; f0 < F; f0 += 4 * 32) {
-      unsigned long long raw[4];
+  for (int b = 0; b < NB; ++b) { Fh[b] = 0.f; Fl[b] = 0.f; }
+  const int64_t u = chunk * kUnitThreads + t;
+  int64_t cs = 0;
+  if (u < S * nseg) {
+    const int64_t s = u / nseg, g = u - s * nseg;
+    const int64_t fs = g * seg;
+    const int n = (int)(F - fs < seg ? F - fs : seg);
+    const unsigned long long* row = img + s * F + fs;
+    for (int i = 0; i < n; ++i) {
+      float th, tl;
+      f64_to_ff(__ldg(row + i), th, tl);
+      if (th == 0.f && tl == 0.f) continue;
+      const float c = (float)(fs + i - off_f);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int64_t f = f0 + q * 32;
-        raw[q] = f < F ? __ldg(row + f) : 0ull;
+      for (int b = 0; b < NB; ++b) {
+        ff_add(Fh[b], Fl[b], th, tl);
+        if (b < K) ff_mul_f(th, tl, c, th, tl);
       }
+    }
+    cs = s - off_s;
+  }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float th, tl;
-        f64_to_ff(raw[q], th, tl);
-        if (th == 0.f && tl == 0.f) continue;
-        const float c = (float)(f0 + q * 32 - off_f);
+  for (int b = 0; b < NB; ++b) Fs[t][b] = make_float2(Fh[b], Fl[b]);
+  Cs[t] = cs;
+  __syncthreads();
+
+  // 2. fold: thread (b, chunk c) takes a contiguous range of segments, sums
+  // the segments of each row, and adds s^a F_b(row) for a <= K - b
+  if (t < NB * CH) {
+    const int b = t / CH, c = t - b * CH;
+    constexpr int per = (kUnitThreads + CH - 1) / CH;
+    const int u0 = c * per, u1 = (u0 + per < kUnitThreads) ? u0 + per : kUnitThreads;
+    float Th[NB], Tl[NB];
 #pragma unroll
-        for (int b = 0; b <= K; ++b) {
-          ff_add(Fh[b], Fl[b], th, tl);
-          if (b < K) ff_mul_f(th, tl, c, th, tl);
+    for (int a = 0; a < NB; ++a) { Th[a] = 0.f; Tl[a] = 0.f; }
+    auto fold = [&](float ph, float pl, int64_t srow) {
+      const float sv = (float)srow;
+      ff_add(Th[0], Tl[0], ph, pl);
+#pragma unroll
+      for (int a = 1; a < NB; ++a) {
+        if (a > K - b) break;
+        ff_mul_f(ph, pl, sv, ph, pl);
+        ff_add(Th[a], Tl[a], ph, pl);
+      }
+    };
+    if (u0 < u1) {
+      float ch = Fs[u0][b].x, cl = Fs[u0][b].y;
+      int64_t cur_s = Cs[u0];
+      for (int uu = u0 + 1; uu < u1; ++uu) {
+        if (Cs[uu] == cur_s) {
+          ff_add(ch, cl, Fs[uu][b].x, Fs[uu][b].y);
+        } else {
+          fold(ch, cl, cur_s);
+          ch = Fs[uu][b].x;
+          cl = Fs[uu][b].y;
+          cur_s = Cs[uu];
         }
       }
+      fold(ch, cl, cur_s);
     }
 #pragma unroll
-    for (int b = 0; b <= K; ++b) {
-#pragma unroll
-      for (int m = 16; m >= 1; m >>= 1) {
-        float oh = __shfl_xor_sync(0xffffffffu, Fh[b], m);
-        float ol = __shfl_xor_sync(0xffffffffu, Fl[b], m);
-        ff_add(Fh[b], Fl[b], oh, ol);
-      }
-    }
-    const float cs = (float)(s - off_s);
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      if (pa[t] < 0) continue;
-      float fh = 0.f, fl = 0.f;
-#pragma unroll
-      for (int b = 0; b <= K; ++b)
-        if (b == pb[t]) { fh = Fh[b]; fl = Fl[b]; }
-      for (int e = 0; e < pa[t]; ++e) ff_mul_f(fh, fl, cs, fh, fl);
-      ff_add(Th[t], Tl[t], fh, fl);
-    }
+    for (int a = 0; a < NB; ++a) part[b][c][a] = make_float2(Th[a], Tl[a]);
   }
-
-  __shared__ float2 red[kWarps][64];
-  red[warp][lane] = make_float2(Th[0], Tl[0]);
-  red[warp][lane + 32] = make_float2(Th[1], Tl[1]);
   __syncthreads();
-  if (warp == 0) {
-    for (int t = 0; t < 2; ++t) {
-      const int idx = lane + 32 * t;
-      if (idx >= p.npairs) continue;
-      float ah = 0.f, al = 0.f;
-      for (int w = 0; w < kWarps; ++w) ff_add(ah, al, red[w][idx].x, red[w][idx].y);
-      static_cast<float2*>(p.partials)[(int64_t)blk * p.npairs + idx] = make_float2(ah, al);
-    }
+
+  // 3. pair (a, b), number n (n + 1) / 2 + b with n = a + b, sums the chunks
+  for (int j = t; j < p.npairs; j += kUnitThreads) {
+    int n = 0;
+    while ((n + 1) * (n + 2) / 2 <= j) ++n;
+    const int b = j - n * (n + 1) / 2, a = n - b;
+    float ah = 0.f, al = 0.f;
+    for (int c = 0; c < CH; ++c) ff_add(ah, al, part[b][c][a].x, part[b][c][a].y);
+    static_cast<float2*>(p.partials)[(int64_t)blk * p.npairs + j] = make_float2(ah, al);
   }
 }
 
-// Pixels per row segment of integer images: 16 .. 128, the largest power of
+// Pixels per row segment: 16 .. 128, the largest power of
 // two that still gives about 78 K segments (16 warps per SM) over all images.
 int int_seg_len(const ImageSet& set) {
   int64_t pixels = 0;
@@ -332,19 +343,15 @@ int int_seg_len(const ImageSet& set) {
   return seg;
 }
 
-// CTAs of step 2 per image: float images take kRowsPerBlock rows per CTA,
-// integer images kUnitThreads row segments per CTA.
+// CTAs of step 2 per image: kUnitThreads row segments per CTA.
 int64_t blocks_of(const ImageSet& set, bool is_float, int64_t* base) {
+  (void)is_float;  // both element types use the same segments
+  const int64_t seg = int_seg_len(set);
   int64_t at = 0;
   for (int k = 0; k < set.P; ++k) {
     if (base) base[k] = at;
-    if (is_float) {
-      at += (set.S[k] + kRowsPerBlock - 1) / kRowsPerBlock;
-    } else {
-      const int64_t seg = int_seg_len(set);
-      const int64_t units = set.S[k] * ((set.F[k] + seg - 1) / seg);
-      at += (units + kUnitThreads - 1) / kUnitThreads;
-    }
+    const int64_t units = set.S[k] * ((set.F[k] + seg - 1) / seg);
+    at += (units + kUnitThreads - 1) / kUnitThreads;
   }
   if (base) base[set.P] = at;
   return at;
@@ -374,7 +381,7 @@ cudaError_t launch_image_moments(const void* images, const ImageSet& set, int K,
   switch (K) {
 #define DPMA_K2_CASE(k)                                                   \
   case k:                                                                 \
-    if (is_float) k2_f32_kernel<k><<<(unsigned)nblk, kThreads, 0, st>>>(p); \
+    if (is_float) k2_f32_seg_kernel<k><<<(unsigned)nblk, kUnitThreads, 0, st>>>(p); \
     else k2_int_cascade_kernel<k><<<(unsigned)nblk, kUnitThreads, 0, st>>>(p); \
     break;
     DPMA_K2_CASE(0) DPMA_K2_CASE(1) DPMA_K2_CASE(2) DPMA_K2_CASE(3) DPMA_K2_CASE(4)
