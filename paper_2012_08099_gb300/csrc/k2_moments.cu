@@ -8,7 +8,7 @@
 // each image (its DRT listing); on a GPU the separable power sums above are
 // cheaper and exact, and they give identical results.
 //
-// Integer images: one thread per row segment of kSegLen pixels runs
+// Integer images: one thread per row segment of 16-128 pixels runs
 // cascaded sums (additions only) and converts them exactly to the
 // segment's power sums F_b; the CTA then folds s^a F_b over its segments.
 // Float images (doubles): the same segments; each double is split into a
