@@ -370,15 +370,17 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
   // takes tile b % nxt and the (b / nxt)-th of cpt equal ranges of that
   // tile's (band, z) units, so the nxt CTAs of consecutive indexes stream
   // the same rows at the same z and together read whole rows of the volume.
-  int64_t ub, ue;
+  // unit, slice and step counters are 32-bit (the launcher checks that the
+  // units fit): 64-bit ones pushed the float kernels into spills
+  int ub, ue;
   if (p.cpt > 0) {
     const int64_t tile = blockIdx.x % p.nxt, c = blockIdx.x / p.nxt;
     const int64_t W = p.nbands * p.nz;
-    ub = tile * W + W * c / p.cpt;
-    ue = tile * W + W * (c + 1) / p.cpt;
+    ub = (int)(tile * W + W * c / p.cpt);
+    ue = (int)(tile * W + W * (c + 1) / p.cpt);
   } else {
-    ub = p.units * (int64_t)blockIdx.x / gridDim.x;
-    ue = p.units * (int64_t)(blockIdx.x + 1) / gridDim.x;
+    ub = (int)(p.units * (int64_t)blockIdx.x / gridDim.x);
+    ue = (int)(p.units * (int64_t)(blockIdx.x + 1) / gridDim.x);
   }
 
   for (int i = tid; i < 2 * X::ES * PW; i += NT) xb[i] = (A)0;
@@ -391,16 +393,16 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
   __syncthreads();
 
   // unit -> (tile x0, band y0, z); units run z fastest, then band, then tile
-  const int64_t zbeg = p.z0, zend = p.z0 + p.nz;
-  auto decode = [&](int64_t u, int64_t& x0, int64_t& y0, int64_t& z) {
-    const int64_t seg = u / p.nz;
-    z = zbeg + u % p.nz;
+  const int zbeg = (int)p.z0, zend = (int)(p.z0 + p.nz);
+  auto decode = [&](int u, int& x0, int& y0, int& z) {
+    const int seg = u / (int)p.nz;
+    z = zbeg + u % (int)p.nz;
     y0 = (seg % p.nbands) * BY;
     x0 = (seg / p.nbands) * XT;
   };
 
   // Producer cursor, kept by thread 0, which issues every copy.
-  int64_t pc_x0 = 0, pc_y0 = 0, pc_z = 0;
+  int pc_x0 = 0, pc_y0 = 0, pc_z = 0;
   if constexpr (TMA) {
     if (tid == 0) decode(ub, pc_x0, pc_y0, pc_z);
   }
@@ -614,13 +616,13 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
   int pend_sb = 0;
   int64_t pend_z = 0;
   bool aborted = false;
-  int64_t s = 0;   // CTA step counter
-  int64_t u = ub;  // next unit
+  int s = 0;   // CTA step counter
+  int u = ub;  // next unit
   while (u < ue && !aborted) {
     // one segment: a (tile, band) streamed over z in [za, zb)
-    int64_t x0, y0, za;
+    int x0, y0, za;
     decode(u, x0, y0, za);
-    const int64_t zb = (zend - za) < (ue - u) ? zend : za + (ue - u);
+    const int zb = (zend - za) < (ue - u) ? zend : za + (ue - u);
     const int64_t xs = x0 + xl, yt = y0 + yl;
     // which of the thread's rows and columns hold voxels
     const int ncol = (int)((L - xs) <= 0 ? 0 : ((L - xs) < R ? (L - xs) : R));
@@ -680,7 +682,7 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
         }
       }
     };
-    int64_t z = za;
+    int z = za;
     while (z < zb && !aborted) {
 #pragma unroll
     for (int j = 0; j < R; ++j) {  // unrolled so window slots are static: j == z % R
@@ -1098,6 +1100,7 @@ cudaError_t launch_t(const ProjectArgs& a, cudaStream_t st) {
   p.nbands = (a.M + BY - 1) / BY;
   p.nxt = (a.L + XT - 1) / XT;
   p.units = p.nxt * p.nbands * p.nz;
+  if (p.units >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;  // 32-bit unit counters
   p.set = a.set;
   p.images = a.images;
   p.status = a.status;
