@@ -354,6 +354,14 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
   A* mb6 = reinterpret_cast<A*>(take(sizeof(A) * PW * 2 * TY * XT));
   A* xb = reinterpret_cast<A*>(take(sizeof(A) * PW * 2 * X::ES));       // [2][ES]
   int4* roles = reinterpret_cast<int4*>(take(sizeof(int4) * NTASK));
+  // float volumes with seven or more images keep image 0's TwoSum pairs in
+  // shared memory ([2 * BYT * R2][NT], one column per thread, conflict-free)
+  // instead of registers: image 0 never moves between threads, and the 16
+  // registers it frees remove most spills (measured 536 -> 515 us at K=6;
+  // with fewer images the registers are not short and it measured slower)
+  constexpr bool kImg0Smem = FL && P >= 7;
+  uint64_t* s0 =
+      kImg0Smem ? reinterpret_cast<uint64_t*>(take(sizeof(uint64_t) * 2 * BYT * (R / 2) * NT)) : nullptr;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -441,7 +449,13 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
       for (int r = 0; r < BYT; ++r)
 #pragma unroll
         for (int c = 0; c < R2; ++c) {
-          P0h[r][c] = P0l[r][c] = P5h[r][c] = P5l[r][c] = P6h[r][c] = P6l[r][c] = 0;
+          if constexpr (kImg0Smem) {
+            s0[(r * R2 + c) * NT + tid] = 0;
+            s0[(BYT * R2 + r * R2 + c) * NT + tid] = 0;
+          } else {
+            P0h[r][c] = P0l[r][c] = 0;
+          }
+          P5h[r][c] = P5l[r][c] = P6h[r][c] = P6l[r][c] = 0;
         }
 #pragma unroll
       for (int q = 0; q < R; ++q)
@@ -459,8 +473,16 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
   clear_state();
   // window pixel (value, compensation) by image, in the scalar index space
   auto g0 = [&](int r, int c, float& lo) -> A {
-    if constexpr (FL) { lo = half_of(P0l[r][c / 2], c & 1); return half_of(P0h[r][c / 2], c & 1); }
-    else { lo = 0.f; return a0[r][c]; }
+    if constexpr (kImg0Smem) {
+      lo = half_of(s0[(BYT * R2 + r * R2 + c / 2) * NT + tid], c & 1);
+      return half_of(s0[(r * R2 + c / 2) * NT + tid], c & 1);
+    } else if constexpr (FL) {
+      lo = half_of(P0l[r][c / 2], c & 1);
+      return half_of(P0h[r][c / 2], c & 1);
+    } else {
+      lo = 0.f;
+      return a0[r][c];
+    }
   };
   auto g3 = [&](int r, int q, float& lo) -> A {
     if constexpr (FL) { lo = half_of(P3l[q][r / 2], r & 1); return half_of(P3h[q][r / 2], r & 1); }
@@ -734,7 +756,16 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
         for (int r = 0; r < BYT; ++r)
 #pragma unroll
           for (int cp = 0; cp < R2; ++cp) {
-            ts2(P0h[r][cp], P0l[r][cp], vc[r][cp]);
+            if constexpr (kImg0Smem) {
+              uint64_t* h0 = s0 + (r * R2 + cp) * NT + tid;
+              uint64_t* l0 = s0 + (BYT * R2 + r * R2 + cp) * NT + tid;
+              uint64_t hv = *h0, lv = *l0;
+              ts2(hv, lv, vc[r][cp]);
+              *h0 = hv;
+              *l0 = lv;
+            } else {
+              ts2(P0h[r][cp], P0l[r][cp], vc[r][cp]);
+            }
             if constexpr (H5) ts2(P5h[(r + j) % BYT][cp], P5l[(r + j) % BYT][cp], vc[r][cp]);
             if constexpr (H6)
               ts2(P6h[(r - j + R) % BYT][cp], P6l[(r - j + R) % BYT][cp], vc[r][cp]);
@@ -1112,6 +1143,7 @@ cudaError_t launch_t(const ProjectArgs& a, cudaStream_t st) {
   smem += 3 * rnd(sizeof(Acc) * PW * 2 * TY * XT);  // slot2, mb5, mb6
   smem += rnd(sizeof(Acc) * PW * 2 * X::ES);        // exit buffer
   smem += rnd(sizeof(int4) * X::tasks(P));          // merge roles
+  if (FL && P >= 7) smem += rnd(sizeof(uint64_t) * 2 * C::BYT * (R / 2) * NT);  // image 0
 
   auto kern = k1_project_kernel<T, P, TMA>;
   static bool attr_set = false;  // per instantiation
