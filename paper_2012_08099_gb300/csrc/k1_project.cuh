@@ -662,7 +662,9 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
     auto merge_step = [&](int msb, int64_t mz) {
       // (a) image 2, one quarter of a column's TY partials per thread
       {
-        const A* e0 = slot2 + ((size_t)(msb * TY + part2 * (TY / 4)) * XT + col2) * PW;
+        // row group r's partials sit at column c ^ (8 * (r / 4)) (see the
+        // writes): the 4 threads of a column then read distinct banks
+        const A* e0 = slot2 + ((size_t)(msb * TY + part2 * (TY / 4)) * XT + (col2 ^ (part2 << 3))) * PW;
         A h = e0[0];
         float l = 0.f;
         if constexpr (FL) l = e0[1];
@@ -798,7 +800,10 @@ __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
       }
       // ---- 3. images in the slice: column sums (2), row sums (1), diagonals (7, 8)
       {
-        A* s2 = slot2 + ((size_t)(sb * TY + ty) * XT + xl) * PW;
+        // column partials of row group ty at column x ^ (8 * (ty / 4)): the
+        // aligned 4-column groups stay contiguous (16-byte stores), and the
+        // merge's reads of row groups 4p .. 4p+3 spread over the banks
+        A* s2 = slot2 + ((size_t)(sb * TY + ty) * XT + (xl ^ ((ty >> 2) << 3))) * PW;
         A rs[BYT];
         float rsc[BYT];
         if constexpr (FL) {
