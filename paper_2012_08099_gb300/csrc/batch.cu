@@ -27,6 +27,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/dpma.h"
@@ -243,6 +244,14 @@ __device__ __forceinline__ void project_volume(const BTask& t, uint32_t* sm, uin
 
 // ---------------------------------------------------------------- step 2
 
+// Units per round of the moment stage: a unit's K + 1 power sums (rt_bytes
+// each) and its row coordinate fit stage buffer 0 (buffer 1 takes a
+// prefetch), at most one unit per thread.
+__host__ __device__ __forceinline__ int moment_units(int nt, int K, int rt_bytes) {
+  const int u = kSlabWords * 4 / ((K + 1) * rt_bytes + 4);
+  return u < nt ? u : nt;
+}
+
 // Geometry of image k (the table of dpma.h): S rows of F pixels, and the
 // offsets that make its coordinates signed (Sec. 5).
 __device__ __forceinline__ void image_geom_dev(const BTask& t, int k, int& S, int& F, int& os, int& of) {
@@ -279,12 +288,71 @@ __device__ __forceinline__ i128 shfl_xor_v(i128 v, int m) {
   return (i128)(((u128)h2 << 64) | l2);
 }
 
+__constant__ StirlingTable c_stir_b = make_stirling();
+
+template <typename UT>
+__device__ __forceinline__ UT ring_of(int64_t v) {
+  if constexpr (sizeof(UT) == 16) return (UT)(i128)v;
+  else return (UT)v;
+}
+
+// Power sums R_b = sum_f I(f) (f - of)^b, b <= KK, of the interleaved
+// segment f = g, g + nseg, ... < F of one image row, by cascaded sums.  For
+// its n pixels I_0 .. I_{n-1}, running A_0 += I_i, A_1 += A_0, ...,
+// A_KK += A_{KK-1} leaves A_j = sum_w w^(j)/j! I with w = n - i and w^(j)
+// the rising factorial, so Q_b = sum_w w^b I = sum_j (-1)^(b-j) S(b,j) j! A_j
+// (Stirling numbers of the second kind).  The signed coordinate is
+// f - of = D - nseg w with D = g + nseg n - of, so R_b = sum_k C(b,k)
+// D^(b-k) (-nseg)^k Q_k, built by the Pascal recurrence.  Every step is ring
+// arithmetic modulo 2^64 (UT = uint64_t) or 2^128, exact because each R_b
+// fits RT (the host's bound).  Per pixel: KK + 1 additions, no products.
+template <int KK, typename UT, bool WIDE>
+__device__ __forceinline__ void seg_power_sums(const uint32_t* sm, int row, int g, int nseg,
+                                               int F, int of, UT* R) {
+  UT A[KK + 1];
+#pragma unroll
+  for (int j = 0; j <= KK; ++j) A[j] = 0;
+  for (int f = g; f < F; f += nseg) {
+    A[0] += (UT)pix_get<WIDE>(sm, row + f);
+#pragma unroll
+    for (int j = 1; j <= KK; ++j) A[j] += A[j - 1];
+  }
+  const int n = (F - g + nseg - 1) / nseg;
+  const UT step = (UT)0 - (UT)(uint32_t)nseg;  // -nseg in the ring
+  UT sc = 1;
+#pragma unroll
+  for (int b = 0; b <= KK; ++b) {
+    UT q = 0;
+#pragma unroll
+    for (int j = 0; j <= b; ++j) q += ring_of<UT>(c_stir_b.v[b][j]) * A[j];
+    R[b] = q * sc;
+    sc *= step;
+  }
+  const UT D = ring_of<UT>((int64_t)g + (int64_t)nseg * n - of);
+#pragma unroll
+  for (int i = 1; i <= KK; ++i)
+#pragma unroll
+    for (int b = KK; b >= i; --b) R[b] += D * R[b - 1];
+}
+
+// One unit of the moment stage: its power sums into dst[0..K].
+template <int KK, typename RT, bool WIDE>
+__device__ __forceinline__ void unit_sums(const uint32_t* sm, int row, int g, int nseg, int F,
+                                          int of, RT* dst) {
+  using UT = typename std::conditional<sizeof(RT) == 16, u128, uint64_t>::type;
+  UT R[KK + 1];
+  seg_power_sums<KK, UT, WIDE>(sm, row, g, nseg, F, of, R);
+#pragma unroll
+  for (int b = 0; b <= KK; ++b) dst[b] = (RT)R[b];
+}
+
 // 2-D moments T_ab (a + b <= K, signed coordinates) of every image of one
 // volume held in shared memory (Eq. 1 with the origin shift of Sec. 5), in
 // rounds of at most U units:
 //  1. unit u = (image k, row s, segment g): row s of image k is cut into
 //     nseg_k interleaved segments of about Lseg pixels; the unit's partial
-//     power sums R_b = sum over its pixels f of I f^b are stored with s;
+//     power sums R_b = sum over its pixels f of I f^b (by cascaded sums) are
+//     stored with s;
 //  2. warp w takes the jobs (k, b) numbered w, w + NW, ...; its lanes run
 //     over image k's units of the round, accumulating s^a R_b for all
 //     a <= K - b along one chain of products, and the warp totals go into
@@ -299,19 +367,15 @@ __device__ __forceinline__ void volume_moments(const BTask& t, const uint32_t* s
   const int K = t.K, P = t.P;
   const int npairs = (K + 1) * (K + 2) / 2;
   const int stride = K + 1;  // RT words per unit
-  constexpr int kScratch = kSlabWords * 4;  // stage buffer 0 (buffer 1 takes a prefetch)
-  const int U = min(NT, (int)(kScratch / (stride * (int)sizeof(RT) + 4)));
+  const int U = moment_units(NT, K, (int)sizeof(RT));
   RT* Rs = static_cast<RT*>(scratch);
   int* Ss = reinterpret_cast<int*>(Rs + (size_t)U * stride);
   if (threadIdx.x == 0) {
-    int64_t pixels = 0;
     for (int k = 0; k < P; ++k) {
       ImgMeta& m = meta[k];
       image_geom_dev(t, k, m.S, m.F, m.os, m.of);
-      pixels += (int64_t)m.S * m.F;
     }
-    // segment length: all pixels over about U units
-    const int Lseg = (int)(pixels > 4ll * U ? (pixels + U - 1) / U : 4);
+    const int Lseg = t.lseg[NT == 512 ? 1 : 0];  // chosen on the host: one round when possible
     int u = 0;
     for (int k = 0; k < P; ++k) {
       meta[k].nseg = (meta[k].F + Lseg - 1) / Lseg;
@@ -331,29 +395,15 @@ __device__ __forceinline__ void volume_moments(const BTask& t, const uint32_t* s
       const ImgMeta m = meta[k];
       v -= m.ustart;
       const int s = v / m.nseg, g = v - s * m.nseg;
-      RT R[kMaxK + 1];
-#pragma unroll
-      for (int b = 0; b <= kMaxK; ++b) R[b] = 0;
       const int row = t.img_off[k] + s * m.F;
-      for (int f = g; f < m.F; f += m.nseg) {
-        const uint32_t pv = pix_get<WIDE>(sm, row + f);
-        if (pv) {
-          const RT fs = (RT)(f - m.of);
-          RT pw = (RT)pv;
-          R[0] += pw;
-#pragma unroll
-          for (int b = 1; b <= kMaxK; ++b) {
-            if (b > K) break;
-            pw *= fs;
-            R[b] += pw;
-          }
-        }
-      }
       RT* dst = Rs + (size_t)threadIdx.x * stride;
-#pragma unroll
-      for (int b = 0; b <= kMaxK; ++b) {
-        if (b > K) break;
-        dst[b] = R[b];
+      switch (K) {
+#define DPMA_UNIT_CASE(kk) \
+  case kk: unit_sums<kk, RT, WIDE>(sm, row, g, m.nseg, m.F, m.of, dst); break;
+        DPMA_UNIT_CASE(0) DPMA_UNIT_CASE(1) DPMA_UNIT_CASE(2) DPMA_UNIT_CASE(3)
+        DPMA_UNIT_CASE(4) DPMA_UNIT_CASE(5) DPMA_UNIT_CASE(6) DPMA_UNIT_CASE(7)
+        default: unit_sums<8, RT, WIDE>(sm, row, g, m.nseg, m.F, m.of, dst); break;
+#undef DPMA_UNIT_CASE
       }
       Ss[threadIdx.x] = s - m.os;
     }
@@ -681,6 +731,33 @@ void classify(const dpma_volume_desc* descs, int count, Classified* c) {
         t.r64 = bits < 62.0 ? 1 : 0;
         // every 2-D moment and partial sum of absolute terms fits int64
         t.t64 = log2_bound_2d(d.L, d.M, d.N, vmax, d.K) < 62.0 ? 1 : 0;
+        // moment-stage segment length: about all pixels over the units of a
+        // round (at least 4), raised until every unit fits one round (each
+        // round costs a pass of the fold and two barriers) or every row is
+        // one segment
+        int64_t S_[kMaxImages], F_[kMaxImages], pixels = 0, fmax = 1;
+        for (int k = 0; k < P; ++k) {
+          ImageGeom g;
+          image_geom(k, d.L, d.M, d.N, &g);
+          S_[k] = g.S; F_[k] = g.F;
+          pixels += g.S * g.F;
+          fmax = std::max(fmax, g.F);
+        }
+        for (int v = 0; v < 2; ++v) {
+          const int64_t U = moment_units(v ? 512 : 256, d.K, t.r64 ? 8 : 16);
+          int64_t Ls = pixels > 4 * U ? (pixels + U - 1) / U : 4;
+          for (;;) {
+            int64_t units = 0, next = fmax;
+            for (int k = 0; k < P; ++k) {
+              const int64_t ns = (F_[k] + Ls - 1) / Ls;
+              units += S_[k] * ns;
+              if (ns > 1) next = std::min(next, (F_[k] + ns - 2) / (ns - 1));
+            }
+            if (units <= U || Ls >= fmax) break;
+            Ls = std::max(Ls + 1, next);
+          }
+          t.lseg[v] = (int)Ls;
+        }
         t.t_off = c->t_total;
         t.out_off = d.out_offset;
         c->t_total += (int64_t)P * num_2d(d.K);

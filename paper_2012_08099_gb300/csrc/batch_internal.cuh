@@ -19,6 +19,7 @@ struct BTask {
   int t64;    // 1: 2-D moments fit int64
   int words;  // 32-bit words of shared memory the images take
   int zblocks[2];  // z-blocks per projection stage at 256 and 512 threads
+  int lseg[2];     // pixels per row segment of the moment stage at 256 and 512 threads
   int img_off[kMaxImages];  // first pixel of each image (even, in pixel units)
   int64_t t_off;            // first 2-D moment of this volume in T (int128 units)
   int64_t out_off;          // byte offset of this volume's moments in the output

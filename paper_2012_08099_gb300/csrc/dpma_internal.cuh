@@ -37,6 +37,29 @@ inline ImageSet make_image_set(int64_t L, int64_t M, int64_t N, int K, bool /*is
   return s;
 }
 
+// Signed Stirling numbers times factorials, (-1)^(b-j) S(b,j) j! for
+// j <= b <= kMaxK (S: Stirling numbers of the second kind).  They turn the
+// cascaded sums A_j = sum_w w^(j)/j! I (w^(j) the rising factorial) into the
+// power sums sum_w w^b I = sum_j (-1)^(b-j) S(b,j) j! A_j.
+struct StirlingTable {
+  int64_t v[kMaxK + 1][kMaxK + 1];
+};
+constexpr StirlingTable make_stirling() {
+  StirlingTable t{};
+  int64_t S[kMaxK + 1][kMaxK + 1] = {};
+  S[0][0] = 1;
+  for (int b = 1; b <= kMaxK; ++b)
+    for (int j = 1; j <= b; ++j) S[b][j] = j * S[b - 1][j] + S[b - 1][j - 1];
+  for (int b = 0; b <= kMaxK; ++b) {
+    int64_t fact = 1;
+    for (int j = 0; j <= b; ++j) {
+      if (j > 0) fact *= j;
+      t.v[b][j] = ((b - j) & 1 ? -1 : 1) * S[b][j] * fact;
+    }
+  }
+  return t;
+}
+
 // ---------------- float-float helpers (error-free transformations) ----------
 
 // s + e == a + b exactly (Knuth's TwoSum, 6 flops, no ordering condition).

@@ -49,24 +49,6 @@ struct K2Params {
 constexpr int kSegLenMax = 128;    // pixels per segment at most: A_0 .. A_4 fit in 64 bits
 constexpr int kUnitThreads = 128;  // segments per CTA
 
-struct StirlingTable {
-  int64_t v[kMaxK + 1][kMaxK + 1];  // (-1)^(b-j) S(b,j) j!
-};
-constexpr StirlingTable make_stirling() {
-  StirlingTable t{};
-  int64_t S[kMaxK + 1][kMaxK + 1] = {};
-  S[0][0] = 1;
-  for (int b = 1; b <= kMaxK; ++b)
-    for (int j = 1; j <= b; ++j) S[b][j] = j * S[b - 1][j] + S[b - 1][j - 1];
-  for (int b = 0; b <= kMaxK; ++b) {
-    int64_t fact = 1;
-    for (int j = 0; j <= b; ++j) {
-      if (j > 0) fact *= j;
-      t.v[b][j] = ((b - j) & 1 ? -1 : 1) * S[b][j] * fact;
-    }
-  }
-  return t;
-}
 __constant__ StirlingTable c_stirling = make_stirling();
 
 template <int K>
