@@ -346,6 +346,90 @@ __device__ __forceinline__ void unit_sums(const uint32_t* sm, int row, int g, in
   for (int b = 0; b <= KK; ++b) dst[b] = (RT)R[b];
 }
 
+// Sum of V values over the 32 lanes of a warp by recursive halving: at each
+// of the first levels (lane masks 16, 8, ...) a lane keeps half of its values
+// and adds its partner's copy of that half, so the shuffles per level halve
+// with the values; the last levels are plain butterflies.  On return x[0] is
+// the warp total of value *index (index >= V: an empty slot), held by every
+// lane whose plain-level bits are the same; *owner marks one of them.
+template <int V, typename AT>
+__device__ __forceinline__ void warp_sum_halving(AT (&x)[V], int lane, int* index, bool* owner) {
+  int base = 0, plain = 0;
+  int c = V;
+#pragma unroll
+  for (int lev = 0; lev < 5; ++lev) {
+    const int m = 16 >> lev;
+    if (c > 1) {
+      const int h = (c + 1) / 2;
+      const bool up = (lane & m) != 0;
+#pragma unroll
+      for (int j = 0; j < h; ++j) {
+        const AT hi = (j + h < c) ? x[j + h] : (AT)0;
+        const AT send = up ? x[j] : hi;
+        const AT keep = up ? hi : x[j];
+        x[j] = keep + shfl_xor_v(send, m);
+      }
+      if (up) base += h;
+      c = h;
+    } else {
+      x[0] += shfl_xor_v(x[0], m);
+      plain |= m;
+    }
+  }
+  *index = base;
+  *owner = (lane & plain) == 0;
+}
+
+// Fold of one round of units into the 2-D moments: T_ab += sum over the
+// round's units of image k of s^a R_b.  Job (k, j) takes the powers b1 = j
+// and b2 = KK - j together (b1 = b2 = KK / 2 alone), so an image needs
+// KK / 2 + 1 jobs and each unit's row powers s^a are formed once per job.
+// Its KK + 2 slots: slot i <= KK - b1 is (a = i, b1); slot i > KK - b1 is
+// (a = KK + 1 - i, b2).
+template <int KK, typename RT, typename AT, int NT>
+__device__ __forceinline__ void fold_round(const RT* Rs, const int* Ss, const ImgMeta* meta, int P,
+                                           int u0, int nu, i128* Tacc) {
+  constexpr int NW = NT / 32, V = KK + 2, JP = KK / 2 + 1;
+  constexpr int npairs = (KK + 1) * (KK + 2) / 2, stride = KK + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int job = warp; job < P * JP; job += NW) {
+    const int k = job / JP, b1 = job - k * JP, b2 = KK - b1;
+    const int lo = max(meta[k].ustart - u0, 0), hi = min(meta[k + 1].ustart - u0, nu);
+    if (lo >= hi) continue;  // uniform across the warp
+    const bool pair = b1 < b2;
+    AT acc[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) acc[i] = 0;
+    for (int u = lo + lane; u < hi; u += 32) {
+      const RT* R = Rs + (size_t)u * stride;
+      const AT r1 = (AT)R[b1];
+      const AT r2 = pair ? (AT)R[b2] : (AT)0;
+      const AT sv = (AT)Ss[u];
+      AT sp[KK + 1];
+      sp[0] = 1;
+#pragma unroll
+      for (int a = 1; a <= KK; ++a) sp[a] = sp[a - 1] * sv;
+#pragma unroll
+      for (int i = 0; i < V; ++i) {
+        const bool first = i <= KK - b1;
+        const AT w = first ? sp[i <= KK ? i : 0] : sp[i == 0 ? 0 : KK + 1 - i];
+        acc[i] += (first ? r1 : r2) * w;
+      }
+    }
+    int idx;
+    bool own;
+    warp_sum_halving<V, AT>(acc, lane, &idx, &own);
+    if (own && idx < V) {
+      const bool first = idx <= KK - b1;
+      if (first || pair) {
+        const int a = first ? idx : KK + 1 - idx, b = first ? b1 : b2;
+        // pair (a, b) is number n (n + 1) / 2 + b with n = a + b
+        Tacc[k * npairs + (a + b) * (a + b + 1) / 2 + b] += (i128)acc[0];
+      }
+    }
+  }
+}
+
 // 2-D moments T_ab (a + b <= K, signed coordinates) of every image of one
 // volume held in shared memory (Eq. 1 with the origin shift of Sec. 5), in
 // rounds of at most U units:
@@ -353,17 +437,14 @@ __device__ __forceinline__ void unit_sums(const uint32_t* sm, int row, int g, in
 //     nseg_k interleaved segments of about Lseg pixels; the unit's partial
 //     power sums R_b = sum over its pixels f of I f^b (by cascaded sums) are
 //     stored with s;
-//  2. warp w takes the jobs (k, b) numbered w, w + NW, ...; its lanes run
-//     over image k's units of the round, accumulating s^a R_b for all
-//     a <= K - b along one chain of products, and the warp totals go into
-//     T_ab.
+//  2. the fold (fold_round): warps take the jobs (k, {b, K - b}); their
+//     lanes run over image k's units of the round, accumulating s^a R_b,
+//     and the warp totals go into T_ab.
 // RT holds a row power sum exactly, AT a 2-D moment (int64 when the host's
 // bounds allow, int128 otherwise).
 template <typename RT, typename AT, bool WIDE, int NT>
 __device__ __forceinline__ void volume_moments(const BTask& t, const uint32_t* sm, void* scratch,
                                                i128* Tacc, ImgMeta* meta, i128* Tout) {
-  constexpr int NW = NT / 32;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int K = t.K, P = t.P;
   const int npairs = (K + 1) * (K + 2) / 2;
   const int stride = K + 1;  // RT words per unit
@@ -408,34 +489,13 @@ __device__ __forceinline__ void volume_moments(const BTask& t, const uint32_t* s
       Ss[threadIdx.x] = s - m.os;
     }
     __syncthreads();
-    for (int job = warp; job < P * (K + 1); job += NW) {
-      const int k = job / (K + 1), b = job - k * (K + 1);
-      const int lo = max(meta[k].ustart - u0, 0), hi = min(meta[k + 1].ustart - u0, nu);
-      if (lo >= hi) continue;  // uniform across the warp
-      AT acc[kMaxK + 1];
-#pragma unroll
-      for (int a = 0; a <= kMaxK; ++a) acc[a] = 0;
-      for (int u = lo + lane; u < hi; u += 32) {
-        const RT r = Rs[(size_t)u * stride + b];
-        if (r == 0) continue;
-        AT pw = (AT)r;
-        const int64_t sv = Ss[u];
-        acc[0] += pw;
-#pragma unroll
-        for (int a = 1; a <= kMaxK; ++a) {
-          if (a > K - b) break;
-          pw *= sv;
-          acc[a] += pw;
-        }
-      }
-#pragma unroll
-      for (int a = 0; a <= kMaxK; ++a) {
-        if (a > K - b) break;
-#pragma unroll
-        for (int mk = 16; mk >= 1; mk >>= 1) acc[a] += shfl_xor_v(acc[a], mk);
-        // pair (a, b) is number n (n + 1) / 2 + b with n = a + b
-        if (lane == 0) Tacc[k * npairs + (a + b) * (a + b + 1) / 2 + b] += (i128)acc[a];
-      }
+    switch (K) {
+#define DPMA_FOLD_CASE(kk) \
+  case kk: fold_round<kk, RT, AT, NT>(Rs, Ss, meta, P, u0, nu, Tacc); break;
+      DPMA_FOLD_CASE(0) DPMA_FOLD_CASE(1) DPMA_FOLD_CASE(2) DPMA_FOLD_CASE(3)
+      DPMA_FOLD_CASE(4) DPMA_FOLD_CASE(5) DPMA_FOLD_CASE(6) DPMA_FOLD_CASE(7)
+      default: fold_round<8, RT, AT, NT>(Rs, Ss, meta, P, u0, nu, Tacc); break;
+#undef DPMA_FOLD_CASE
     }
     __syncthreads();
   }
