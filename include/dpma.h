@@ -245,12 +245,15 @@ typedef struct dpma_batch dpma_batch;
  * volume): validates every descriptor on the host, uploads the task table
  * and allocates the plan's device buffers (synchronous).  Volumes whose
  * images fit on chip (integer element types, a z-slice of at most 24 KB,
- * images within shared memory) run in one persistent fused launch: projection and 2-D
- * moments per volume in shared memory, then one batched combine launch.
- * The others (float32 or larger volumes) run through the single-volume
- * pipeline, one after another on the same stream.  With
- * DPMA_BATCH_AUTOTUNE the volumes must already hold their data: the fused
- * launch is timed at 256 and 512 threads per CTA and the faster is kept.
+ * images within shared memory) run in persistent fused launches: projection
+ * and 2-D moments per volume in shared memory, then one batched combine
+ * launch.  The fused volumes whose footprint lets two 256-thread CTAs share
+ * an SM run in a second launch after the larger ones (one launch when all
+ * are alike).  The others (float32 or larger volumes) run through the
+ * single-volume pipeline, one after another on the same stream.  With
+ * DPMA_BATCH_AUTOTUNE the volumes must already hold their data: the split
+ * and a single launch are timed at 256 and 512 threads per CTA and the
+ * fastest is kept.
  * The descriptors' pointers are kept by the plan until dpma_batch_destroy.
  * Errors: DPMA_ERR_INVALID_ARG (null pointers, bad descriptor, unknown
  * flag), DPMA_ERR_OVERFLOW (a volume's moments could leave int128),
@@ -276,9 +279,11 @@ dpma_status dpma_batch_run(dpma_batch* plan, void* out, void* stream);
 dpma_status dpma_batch_status(dpma_batch* plan, void* stream);
 
 /*
- * Plan facts for tests and tuning: what = 0 volumes in the fused launch,
- * 1 volumes on the single-volume path, 2 threads per CTA, 3 CTAs of the
- * fused launch, 4 its dynamic shared memory in bytes; -1 for a bad query.
+ * Plan facts for tests and tuning: what = 0 volumes in the fused launches,
+ * 1 volumes on the single-volume path, 2 threads per CTA, 3 CTAs and 4
+ * dynamic shared memory in bytes of the first fused launch, 5 fused
+ * launches (0, 1 or 2), 6 volumes, 7 threads per CTA and 8 CTAs of the
+ * second; -1 for a bad query.
  */
 int dpma_batch_info(const dpma_batch* plan, int what);
 

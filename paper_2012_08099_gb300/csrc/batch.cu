@@ -518,7 +518,7 @@ __device__ __forceinline__ void moments_any(const BTask& t, const uint32_t* sm, 
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT, 1) batch_fused_kernel(FusedParams p) {
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) batch_fused_kernel(FusedParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   i128* Tacc = reinterpret_cast<i128*>(smem_raw);
   __shared__ ImgMeta meta[kMaxImages + 1];
@@ -845,10 +845,8 @@ size_t fused_smem(size_t max_words) {
   return (size_t)kPartBytes + 2 * (size_t)kSlabWords * 4 + (max_words + kSlackWords) * 4;
 }
 
-int fused_grid(size_t smem, int threads, int ntasks) {
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+int fused_per_sm(size_t smem, int threads) {
+  int per_sm = 0;
   cudaError_t e;
   if (threads == 512) {
     set_smem<512>(smem);
@@ -857,8 +855,28 @@ int fused_grid(size_t smem, int threads, int ntasks) {
     set_smem<256>(smem);
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_fused_kernel<256>, 256, smem);
   }
-  if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-  return std::max(1, std::min(sms * per_sm, ntasks));
+  return (e != cudaSuccess || per_sm < 1) ? 1 : per_sm;
+}
+
+int fused_grid(size_t smem, int threads, int ntasks) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(1, std::min(sms * fused_per_sm(smem, threads), ntasks));
+}
+
+size_t two_cta_smem_limit() {
+  int dev = 0, per_sm = 0, reserved = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, batch_fused_kernel<256>);
+  const int64_t lim = (int64_t)per_sm / 2 - reserved - (int64_t)fa.sharedSizeBytes;
+  size_t out = lim > 0 ? (size_t)lim : 0;
+  // the occupancy calculator has the last word
+  while (out > 0 && fused_per_sm(out, 256) < 2) out = out > 1024 ? out - 1024 : 0;
+  return out;
 }
 
 cudaError_t prepare_plans() {
@@ -867,29 +885,33 @@ cudaError_t prepare_plans() {
 }
 
 cudaError_t enqueue_fused(const BTask* d_tasks, const int* d_order, int n, int max_K,
-                          int* d_counter, i128* d_T, size_t smem, int threads, int grid,
+                          int* d_counters, i128* d_T, const FusedGroup* groups, int ngroups,
                           void* out, int* d_status, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const DevPlans* dp = nullptr;
   cudaError_t e = plans_for_device(&dp);
   if (e != cudaSuccess) return e;
-  FusedParams p{};
-  p.tasks = d_tasks;
-  p.order = d_order;
-  p.ntasks = n;
-  p.counter = d_counter;
-  p.T = d_T;
-  if (threads == 512) {
-    e = set_smem<512>(smem);
+  for (int g = 0; g < ngroups; ++g) {
+    const FusedGroup& G = groups[g];
+    if (G.count <= 0) continue;
+    FusedParams p{};
+    p.tasks = d_tasks;
+    p.order = d_order + G.first;
+    p.ntasks = G.count;
+    p.counter = d_counters + g;
+    p.T = d_T;
+    if (G.threads == 512) {
+      e = set_smem<512>(G.smem);
+      if (e != cudaSuccess) return e;
+      batch_fused_kernel<512><<<G.grid, 512, G.smem, st>>>(p);
+    } else {
+      e = set_smem<256>(G.smem);
+      if (e != cudaSuccess) return e;
+      batch_fused_kernel<256><<<G.grid, 256, G.smem, st>>>(p);
+    }
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    batch_fused_kernel<512><<<grid, 512, smem, st>>>(p);
-  } else {
-    e = set_smem<256>(smem);
-    if (e != cudaSuccess) return e;
-    batch_fused_kernel<256><<<grid, 256, smem, st>>>(p);
   }
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   BCombParams cp{};
   cp.tasks = d_tasks;
   cp.ntasks = n;
@@ -920,12 +942,14 @@ struct dpma_batch {
   batch::Classified cls;
   BTask* d_tasks = nullptr;
   int* d_order = nullptr;
-  int* d_counter = nullptr;
+  int* d_counter = nullptr;  // one queue counter per fused group
   int* d_status = nullptr;
   i128* d_T = nullptr;
-  size_t smem = 0;
-  int threads = 512;
-  int grid = 0;
+  batch::FusedGroup groups[batch::kMaxGroups];
+  int ngroups = 0;
+  std::vector<int> order;  // fused queue: large-footprint volumes, then the others, each largest first
+  int n_over = 0;          // volumes whose footprint rules out two CTAs per SM
+  int sms = 1;
   void* d_ws = nullptr;  // workspace of the single-volume path
   size_t ws_bytes = 0;
 };
@@ -943,16 +967,51 @@ void free_plan(dpma_batch* b) {
   delete b;
 }
 
+// Fused launches of plan b: order[0 .. X) in one launch of nt0-thread CTAs
+// and order[X .. n) in a second of 256-thread CTAs (none when X = n), each
+// with the shared memory of its largest footprint.
+void set_split(dpma_batch* b, int X, int nt0) {
+  const std::vector<BTask>& tasks = b->cls.tasks;
+  const int n = (int)b->order.size();
+  size_t w0 = 0, w1 = 0;
+  for (int i = 0; i < n; ++i) {
+    const size_t w = (size_t)tasks[b->order[i]].words;
+    if (i < X) w0 = std::max(w0, w);
+    else w1 = std::max(w1, w);
+  }
+  b->ngroups = 0;
+  if (X > 0) {
+    batch::FusedGroup& g = b->groups[b->ngroups++];
+    g.first = 0; g.count = X; g.smem = batch::fused_smem(w0); g.threads = nt0;
+    g.grid = batch::fused_grid(g.smem, nt0, X);
+  }
+  if (X < n) {
+    batch::FusedGroup& g = b->groups[b->ngroups++];
+    g.first = X; g.count = n - X; g.smem = batch::fused_smem(w1); g.threads = 256;
+    g.grid = batch::fused_grid(g.smem, 256, n - X);
+  }
+}
+
+// Split used without autotuning: the large-footprint volumes and then the
+// largest of the rest up to eight volumes per SM in the first launch (on
+// 4096 ROI masks of sizes 8..96, 2, 4, 8 volumes per SM or one launch
+// measured 0.468, 0.424, 0.382 and 0.419 ms).
+int default_split(const dpma_batch* b) {
+  const int n = (int)b->order.size();
+  if (b->n_over == 0) return 0;
+  return std::min(n, std::max(b->n_over, 8 * b->sms));
+}
+
 dpma_status enqueue_batch(dpma_batch* b, void* out, cudaStream_t st, bool singles = true) {
   unsigned char* o = static_cast<unsigned char*>(out);
   cudaError_t e = cudaMemsetAsync(b->d_status, 0, sizeof(int), st);
   if (e != cudaSuccess) return bfail(DPMA_ERR_CUDA, std::string("clear status: ") + cudaGetErrorString(e));
   const int n = (int)b->cls.tasks.size();
   if (n > 0) {
-    e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st);
+    e = cudaMemsetAsync(b->d_counter, 0, sizeof(int) * batch::kMaxGroups, st);
     if (e == cudaSuccess)
-      e = batch::enqueue_fused(b->d_tasks, b->d_order, n, b->cls.max_K, b->d_counter, b->d_T, b->smem,
-                               b->threads, b->grid, out, b->d_status, st);
+      e = batch::enqueue_fused(b->d_tasks, b->d_order, n, b->cls.max_K, b->d_counter, b->d_T,
+                               b->groups, b->ngroups, out, b->d_status, st);
     if (e != cudaSuccess)
       return bfail(DPMA_ERR_CUDA, std::string("batched kernels: ") + cudaGetErrorString(e));
   }
@@ -1025,21 +1084,38 @@ dpma_status dpma_batch_create(const dpma_volume_desc* descs, int count, int flag
   if (e != cudaSuccess) return oom(e, "batch status");
   const std::vector<BTask>& tasks = b->cls.tasks;
   if (!tasks.empty()) {
-    const std::vector<int> order = batch::lpt_order(tasks);
+    // Two launches when the batch mixes footprints: the volumes whose launch
+    // fits two 256-thread CTAs per SM run after the others in a launch that
+    // keeps two volumes in flight per SM (their barriers and latency-bound
+    // moment stages overlap); each group takes its volumes largest first.
+    // The first launch also takes the largest of the small-footprint volumes
+    // until it holds a few volumes per SM, so that its tail stays short.
+    const std::vector<int> lpt = batch::lpt_order(tasks);
+    const size_t small_limit = batch::two_cta_smem_limit();
+    std::vector<int> small;
+    b->order.clear();
+    for (int i : lpt) {
+      if (batch::fused_smem((size_t)tasks[i].words) <= small_limit) small.push_back(i);
+      else b->order.push_back(i);
+    }
+    b->n_over = (int)b->order.size();
+    b->order.insert(b->order.end(), small.begin(), small.end());
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    b->sms = std::max(1, sms);
+    set_split(b, default_split(b), 512);
     e = cudaMalloc(&b->d_tasks, sizeof(BTask) * tasks.size());
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_order, sizeof(int) * order.size());
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_order, sizeof(int) * b->order.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int) * batch::kMaxGroups);
     if (e == cudaSuccess)
       e = cudaMalloc(&b->d_T, sizeof(i128) * (size_t)std::max<int64_t>(1, b->cls.t_total));
     if (e != cudaSuccess) return oom(e, "batch buffers");
     e = cudaMemcpy(b->d_tasks, tasks.data(), sizeof(BTask) * tasks.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-      e = cudaMemcpy(b->d_order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice);
+      e = cudaMemcpy(b->d_order, b->order.data(), sizeof(int) * b->order.size(),
+                     cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = batch::prepare_plans();
     if (e != cudaSuccess) return oom(e, "batch upload");
-    b->smem = batch::fused_smem(b->cls.max_words);
-    b->threads = 512;
-    b->grid = batch::fused_grid(b->smem, 512, (int)tasks.size());
   }
   if (!b->cls.single.empty()) {
     size_t ws = 0;
@@ -1055,7 +1131,9 @@ dpma_status dpma_batch_create(const dpma_volume_desc* descs, int count, int flag
   }
 
   if ((flags & DPMA_BATCH_AUTOTUNE) && !tasks.empty()) {
-    // time both CTA sizes of the fused launch on the real inputs, keep the faster
+    // time the candidate launch shapes on the real inputs, keep the fastest:
+    // the large-footprint group at 512 or 256 threads, or all volumes in one
+    // launch at either size
     void* scratch = nullptr;
     size_t ob = 16;
     for (const dpma_volume_desc& d : b->descs)
@@ -1067,11 +1145,27 @@ dpma_status dpma_batch_create(const dpma_volume_desc* descs, int count, int flag
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    // candidates: the split after X volumes (X = the large-footprint ones,
+    // or 2 to 24 volumes per SM) with the first launch at 512 or 256
+    // threads, or all volumes in one launch (X = n)
+    std::vector<std::vector<batch::FusedGroup>> cand;
+    const int n = (int)tasks.size();
+    std::vector<int> splits = {b->n_over, 2 * b->sms, 4 * b->sms, 8 * b->sms,
+                               12 * b->sms, 16 * b->sms, 24 * b->sms, n};
+    std::sort(splits.begin(), splits.end());
+    splits.erase(std::unique(splits.begin(), splits.end()), splits.end());
+    for (int X : splits) {
+      if (X < b->n_over || X > n) continue;
+      for (int nt : {512, 256}) {
+        set_split(b, X, nt);
+        cand.emplace_back(b->groups, b->groups + b->ngroups);
+      }
+    }
     float best = 1e30f;
-    int best_nt = 512, best_grid = b->grid;
-    for (int nt : {256, 512}) {
-      b->threads = nt;
-      b->grid = batch::fused_grid(b->smem, nt, (int)tasks.size());
+    std::vector<batch::FusedGroup> keep(b->groups, b->groups + b->ngroups);
+    for (const auto& c : cand) {
+      std::copy(c.begin(), c.end(), b->groups);
+      b->ngroups = (int)c.size();
       enqueue_batch(b, scratch, st, false);
       cudaEventRecord(e0, st);
       for (int r = 0; r < 3; ++r) enqueue_batch(b, scratch, st, false);
@@ -1079,10 +1173,10 @@ dpma_status dpma_batch_create(const dpma_volume_desc* descs, int count, int flag
       cudaEventSynchronize(e1);
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) { best = ms; best_nt = nt; best_grid = b->grid; }
+      if (ms < best) { best = ms; keep = c; }
     }
-    b->threads = best_nt;
-    b->grid = best_grid;
+    std::copy(keep.begin(), keep.end(), b->groups);
+    b->ngroups = (int)keep.size();
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(st);
@@ -1116,9 +1210,13 @@ int dpma_batch_info(const dpma_batch* plan, int what) {
   switch (what) {
     case 0: return (int)plan->cls.tasks.size();
     case 1: return (int)plan->cls.single.size();
-    case 2: return plan->threads;
-    case 3: return plan->grid;
-    case 4: return (int)plan->smem;
+    case 2: return plan->ngroups ? plan->groups[0].threads : 0;
+    case 3: return plan->ngroups ? plan->groups[0].grid : 0;
+    case 4: return plan->ngroups ? (int)plan->groups[0].smem : 0;
+    case 5: return plan->ngroups;
+    case 6: return plan->ngroups > 1 ? plan->groups[1].count : 0;
+    case 7: return plan->ngroups > 1 ? plan->groups[1].threads : 0;
+    case 8: return plan->ngroups > 1 ? plan->groups[1].grid : 0;
   }
   return -1;
 }

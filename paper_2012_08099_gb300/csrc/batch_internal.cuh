@@ -43,16 +43,31 @@ std::vector<int> lpt_order(const std::vector<BTask>& tasks);
 size_t fused_smem(size_t max_words);
 // CTAs of a fused launch: resident capacity, at most ntasks.
 int fused_grid(size_t smem, int threads, int ntasks);
+// Resident CTAs per SM of a fused launch.
+int fused_per_sm(size_t smem, int threads);
+// Largest dynamic shared memory of a 256-thread fused launch with two CTAs
+// resident per SM.
+size_t two_cta_smem_limit();
 // Packed combine plans of every order 0..8 resident on the current device
 // (built once per device; synchronous the first time).
 cudaError_t prepare_plans();
-// Enqueues the fused projection + 2-D moment launch and the batched combine
-// for n tasks already in device memory, whose highest order is max_K; `out`
-// is the base the tasks' out_off refer to; *d_status becomes 7 if an exact
-// division left a remainder.  d_counter must be zero when the launch starts
-// (the caller clears it).
+
+// One persistent fused launch over the tasks order[first .. first + count).
+struct FusedGroup {
+  int first = 0, count = 0;
+  size_t smem = 0;
+  int threads = 512, grid = 0;
+};
+constexpr int kMaxGroups = 2;
+
+// Enqueues the fused projection + 2-D moment launches of the groups (one
+// after another, each with its own queue counter d_counters[g], which must
+// be zero when the launch starts: the caller clears them) and the batched
+// combine for all n tasks already in device memory, whose highest order is
+// max_K; `out` is the base the tasks' out_off refer to; *d_status becomes 7
+// if an exact division left a remainder.
 cudaError_t enqueue_fused(const BTask* d_tasks, const int* d_order, int n, int max_K,
-                          int* d_counter, i128* d_T, size_t smem, int threads, int grid,
+                          int* d_counters, i128* d_T, const FusedGroup* groups, int ngroups,
                           void* out, int* d_status, cudaStream_t st);
 // Enqueues *dst = max(*dst, *src) on the device.
 cudaError_t enqueue_merge_status(const int* src, int* dst, cudaStream_t st);

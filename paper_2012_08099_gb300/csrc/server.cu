@@ -512,12 +512,15 @@ bool launch_group(dpma_server* s, Group* g, bool fused) {
     e = cudaMemcpyAsync(cdev, chost, tb + ob, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(cdev + tb + ob, 0, 512, st);
     if (e == cudaSuccess) {
-      const size_t smem = batch::fused_smem(c.max_words);
-      const int grid = batch::fused_grid(smem, 512, n);
+      batch::FusedGroup grp;
+      grp.count = n;
+      grp.smem = batch::fused_smem(c.max_words);
+      grp.threads = 512;
+      grp.grid = batch::fused_grid(grp.smem, 512, n);
       e = batch::enqueue_fused(reinterpret_cast<const BTask*>(cdev),
                                reinterpret_cast<const int*>(cdev + tb), n, c.max_K,
                                reinterpret_cast<int*>(cdev + tb + ob),
-                               reinterpret_cast<i128*>(base), smem, 512, grid, base,
+                               reinterpret_cast<i128*>(base), &grp, 1, base,
                                reinterpret_cast<int*>(cdev + tb + ob + 256), st);
     }
     if (e == cudaSuccess)

@@ -168,6 +168,32 @@ def test_config_4096_roi_masks_k4(dpma):
         assert got[i][3] == int((w.sum(axis=(1, 2)) * np.arange(N)).sum())
 
 
+def test_footprint_split_matches_single_volume(dpma):
+    """ROI masks of mixed sizes: the small-footprint volumes run in a second
+    fused launch with two 256-thread CTAs per SM; every result is unchanged."""
+    rb = synth.roi_batch(1600, seed=5)
+    tv = [dev(v) for v in rb.volumes]
+    b = dpma.Batch([t for t, _ in tv], [4] * len(tv), [d for _, d in tv])
+    assert b.info(0) == len(tv) and b.info(5) == 2
+    assert 0 < b.info(6) < len(tv) and b.info(7) == 256
+    out = b.out_buffer()
+    b.run(out)
+    b.status()
+    got = b.values(out)
+    for i in range(0, len(tv), 11):
+        t, d = tv[i]
+        assert got[i] == single(dpma, t, 4, d), i
+    # all small: one launch of 256-thread CTAs
+    small = [dev(v) for v in synth.roi_batch(64, seed=6, size_range=(8, 24)).volumes]
+    bs = dpma.Batch([t for t, _ in small], [3] * len(small), [d for _, d in small])
+    assert bs.info(5) == 1 and bs.info(2) == 256
+    out = bs.out_buffer()
+    bs.run(out)
+    bs.status()
+    for (t, d), g in zip(small, bs.values(out)):
+        assert g == single(dpma, t, 3, d)
+
+
 def test_batch_rejects_bad_descriptors(dpma):
     t, d = dev(synth.uniform_volume((4, 4, 4), np.uint8, seed=1))
     with pytest.raises(dpma.DpmaError) as e:
