@@ -383,7 +383,9 @@ def run_batched(dpma, torch, reps=20):
     return {"workload": "roi_masks_u8_4096_K4", "value": n / (ms_batch * 1e-3),
             "unit": "volume/s", "voxels_per_s": voxels / (ms_batch * 1e-3),
             "ms_per_batch": round(ms_batch, 4), "volumes": n, "voxels": int(voxels),
-            "graph_captured": True, "fused_threads": b.info(2), "fused_ctas": b.info(3),
+            "graph_captured": True, "fused_launches": b.info(5),
+            "fused_threads": b.info(2), "fused_ctas": b.info(3),
+            "second_launch": {"volumes": b.info(6), "threads": b.info(7), "ctas": b.info(8)},
             "per_volume_launches": {"value": n / (ms_single * 1e-3), "unit": "volume/s",
                                     "ms_per_batch": round(ms_single, 3)},
             "speedup_vs_per_volume": round(ms_single / ms_batch, 2),
