@@ -47,8 +47,11 @@ namespace {
 
 // the 2-D moments T_ab of every image of the volume being reduced (int128)
 constexpr int kPartBytes = kMaxImages * kMax2D * 16;
-constexpr int kSlabWords = 6144;
-constexpr int kSlackWords = 4;  // past the last image: zero adds of a ragged chunk  // one z-slice of a fused volume (24 KB), double-buffered
+constexpr int kSlabWords = 6144;  // one stage buffer (24 KB), double-buffered
+constexpr int kChunk = 8;  // voxels of one row per projection position
+// words past the last image: the zero adds of a ragged chunk reach up to
+// kChunk - 1 pixels past a row
+constexpr int kSlackWords = 8;
 constexpr int kSmemLimit = 227 * 1024 - 512;  // dynamic bytes: the rest is static (meta, task id)
 constexpr int kStatusInternal = 7;
 
@@ -108,8 +111,30 @@ __device__ __forceinline__ void add4(uint32_t* sm, int b, uint32_t p01, uint32_t
   }
 }
 
+// Adds the eight consecutive pixels b .. b+7 of one image row, given as the
+// packed pairs p01, p23, q01, q23 (pixels 0-1, 2-3, 4-5, 6-7; every v <
+// 2^16): with 16-bit pixels five shifted words from word b/2, one shared
+// atomic each (no carry crosses a halfword, as in add4).
+template <bool WIDE>
+__device__ __forceinline__ void add8(uint32_t* sm, int b, uint32_t p01, uint32_t p23,
+                                     uint32_t q01, uint32_t q23) {
+  if constexpr (WIDE) {
+    add4<true>(sm, b, p01, p23);
+    add4<true>(sm, b + 4, q01, q23);
+  } else {
+    const int w = b >> 1;
+    const uint32_t sh = (uint32_t)(b & 1) << 4;
+    atomicAdd(sm + w, p01 << sh);
+    atomicAdd(sm + w + 1, __funnelshift_l(p01, p23, sh));
+    atomicAdd(sm + w + 2, __funnelshift_l(p23, q01, sh));
+    atomicAdd(sm + w + 3, __funnelshift_l(q01, q23, sh));
+    atomicAdd(sm + w + 4, __funnelshift_l(q23, 0u, sh));
+  }
+}
+
 // Slices per projection stage: as many as fit in one buffer with the 16-byte
-// alignment head and the two words a chunk load may read past the stage.
+// alignment head and the bytes a chunk load may read past the stage (the
+// aligned words covering a chunk: up to 18 bytes past its last voxel).
 __host__ __device__ __forceinline__ int stage_slices(int64_t slice_bytes, int N) {
   const int64_t g = ((int64_t)(kSlabWords - 8) * 4 - 30) / slice_bytes;
   return (int)(g < 1 ? 1 : (g < N ? g : N));
@@ -143,12 +168,13 @@ __device__ __forceinline__ int fetch_stage(const BTask& t, int z0, uint32_t* dst
 // is processed (a 16-byte block holding a byte of the volume lies in the same
 // mapped page).  Stage 0 arrives in `first` (copied ahead, during the
 // previous volume's moment stage, and complete on entry: it is slab buffer
-// 1); stage s uses slab buffer (s + 1) & 1.  A position is a chunk of four consecutive voxels of one row,
-// (y, c) with x0 = 4c; the stage's slices are split into Zg blocks so that
-// positions x blocks fill the CTA, and a thread walks its position through
-// the z of its block.  Four consecutive voxels of a row land on four
-// consecutive pixels of every image but image 1 (z, y), which takes the
-// chunk's sum; image 0 (y, x) does not move with z and is summed in
+// 1); stage s uses slab buffer (s + 1) & 1.  A position is a chunk of
+// kChunk = 8 consecutive voxels of one row, (y, c) with x0 = 8c; the stage's
+// slices are split into Zg blocks so that positions x blocks fill the CTA,
+// and a thread walks its position through the z of its block.  The chunk's
+// voxels land on eight consecutive pixels of every image but image 1 (z, y),
+// which takes the chunk's sum (eight voxels per atomic: the lanes of one row
+// share that pixel); image 0 (y, x) does not move with z and is summed in
 // registers over the block.  Every shared update is an atomic add; image k's
 // pixel index moves by a constant per z-step.
 template <typename T, bool WIDE, bool MANY, int NT>
@@ -159,7 +185,7 @@ __device__ __forceinline__ void project_volume(const BTask& t, uint32_t* sm, uin
   const int* o = t.img_off;
   const int slice_bytes = L * M * (int)sizeof(T);
   const int G = stage_slices(slice_bytes, N);
-  const int nc = (L + 3) >> 2, npos = M * nc;
+  const int nc = (L + kChunk - 1) / kChunk, npos = M * nc;
   const int Zg = t.zblocks[NT == 512 ? 1 : 0];  // z-blocks per stage
   int head = head0, head_next = 0;
   const uint32_t* cur = first;
@@ -173,7 +199,7 @@ __device__ __forceinline__ void project_volume(const BTask& t, uint32_t* sm, uin
     const int gz = min(G, N - z0), zlen = (gz + Zg - 1) / Zg;
     for (int it = threadIdx.x; it < npos * Zg; it += NT) {
       const int zg = it / npos, pos = it - zg * npos;
-      const int y = pos / nc, x0 = (pos - y * nc) << 2;
+      const int y = pos / nc, x0 = (pos - y * nc) * kChunk;
       const int zs = z0 + zg * zlen, ze = min(z0 + gz, zs + zlen);
       if (zs >= ze) continue;
       const int rem = L - x0;
@@ -183,42 +209,59 @@ __device__ __forceinline__ void project_volume(const BTask& t, uint32_t* sm, uin
       int b3 = o[3] + y * F3 + x0 + zs, b4 = o[4] + y * F3 + x0 - zs + N - 1;
       int b5 = o[5] + (y + zs) * L + x0, b6 = o[6] + (y - zs + N - 1) * L + x0;
       int b7 = o[7] + zs * F7 + x0 + y, b8 = o[8] + zs * F7 + x0 - y + M - 1;
-      uint32_t i0a = 0, i0b = 0, i0c = 0, i0d = 0;  // image 0 over the block
+      // image 0 over the block: packed pairs, or one word per pixel
+      uint32_t i0[WIDE ? 8 : 4] = {};
       for (int z = zs; z < ze; ++z) {
         const uint32_t* W = reinterpret_cast<const uint32_t*>(S + (off & ~3));
         const uint32_t sh = (uint32_t)(off & 3) << 3;
-        uint32_t p01, p23, rs;
+        uint32_t p01, p23, q01, q23, rs;
         if constexpr (sizeof(T) == 1) {
-          uint32_t wv = __funnelshift_r(W[0], W[1], sh);
-          if (rem < 4) wv &= (1u << (rem << 3)) - 1u;
-          p01 = __byte_perm(wv, 0u, 0x4140);
-          p23 = __byte_perm(wv, 0u, 0x4342);
-          rs = __dp4a(wv, 0x01010101u, 0u);
-        } else {  // off is even: the volume and its slices are 2-byte aligned
           const uint32_t w1 = W[1];
-          p01 = __funnelshift_r(W[0], w1, sh);
-          p23 = __funnelshift_r(w1, W[2], sh);
-          if (rem < 4) {
-            if (rem == 1) p01 &= 0xffffu;
-            p23 = rem == 3 ? (p23 & 0xffffu) : 0u;
+          uint32_t wa = __funnelshift_r(W[0], w1, sh), wb = __funnelshift_r(w1, W[2], sh);
+          if (rem < 8) {  // bytes past the row end are zero
+            if (rem < 4) { wa &= (1u << (rem << 3)) - 1u; wb = 0u; }
+            else wb &= (1u << ((rem - 4) << 3)) - 1u;
           }
-          rs = (p01 & 0xffffu) + (p01 >> 16) + (p23 & 0xffffu) + (p23 >> 16);
+          p01 = __byte_perm(wa, 0u, 0x4140);
+          p23 = __byte_perm(wa, 0u, 0x4342);
+          q01 = __byte_perm(wb, 0u, 0x4140);
+          q23 = __byte_perm(wb, 0u, 0x4342);
+          rs = __dp4a(wa, 0x01010101u, __dp4a(wb, 0x01010101u, 0u));
+        } else {  // off is even: the volume and its slices are 2-byte aligned
+          const uint32_t w1 = W[1], w2 = W[2], w3 = W[3];
+          p01 = __funnelshift_r(W[0], w1, sh);
+          p23 = __funnelshift_r(w1, w2, sh);
+          q01 = __funnelshift_r(w2, w3, sh);
+          q23 = __funnelshift_r(w3, W[4], sh);
+          if (rem < 8) {  // halfwords past the row end are zero
+            const uint32_t keep[4] = {p01, p23, q01, q23};
+            uint32_t m[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int lo = 2 * i;  // pixels lo, lo + 1 of the chunk
+              m[i] = rem > lo + 1 ? keep[i] : (rem == lo + 1 ? (keep[i] & 0xffffu) : 0u);
+            }
+            p01 = m[0]; p23 = m[1]; q01 = m[2]; q23 = m[3];
+          }
+          rs = (p01 & 0xffffu) + (p01 >> 16) + (p23 & 0xffffu) + (p23 >> 16) +
+               (q01 & 0xffffu) + (q01 >> 16) + (q23 & 0xffffu) + (q23 >> 16);
         }
         if (rs) {
-          pix_atomic<WIDE>(sm, b1, rs);           // (z, y)
-          add4<WIDE>(sm, b2, p01, p23);           // (z, x)
-          if (P > 3) add4<WIDE>(sm, b3, p01, p23);  // (y, x+z)
-          if (P > 4) add4<WIDE>(sm, b4, p01, p23);  // (y, x-z)
+          pix_atomic<WIDE>(sm, b1, rs);                       // (z, y)
+          add8<WIDE>(sm, b2, p01, p23, q01, q23);             // (z, x)
+          if (P > 3) add8<WIDE>(sm, b3, p01, p23, q01, q23);  // (y, x+z)
+          if (P > 4) add8<WIDE>(sm, b4, p01, p23, q01, q23);  // (y, x-z)
           if constexpr (MANY) {
-            add4<WIDE>(sm, b5, p01, p23);             // (y+z, x)
-            if (P > 6) add4<WIDE>(sm, b6, p01, p23);  // (y-z, x)
-            if (P > 7) add4<WIDE>(sm, b7, p01, p23);  // (z, x+y)
-            if (P > 8) add4<WIDE>(sm, b8, p01, p23);  // (z, x-y)
+            add8<WIDE>(sm, b5, p01, p23, q01, q23);             // (y+z, x)
+            if (P > 6) add8<WIDE>(sm, b6, p01, p23, q01, q23);  // (y-z, x)
+            if (P > 7) add8<WIDE>(sm, b7, p01, p23, q01, q23);  // (z, x+y)
+            if (P > 8) add8<WIDE>(sm, b8, p01, p23, q01, q23);  // (z, x-y)
           }
           if constexpr (WIDE) {
-            i0a += p01 & 0xffffu; i0b += p01 >> 16; i0c += p23 & 0xffffu; i0d += p23 >> 16;
+            i0[0] += p01 & 0xffffu; i0[1] += p01 >> 16; i0[2] += p23 & 0xffffu; i0[3] += p23 >> 16;
+            i0[4] += q01 & 0xffffu; i0[5] += q01 >> 16; i0[6] += q23 & 0xffffu; i0[7] += q23 >> 16;
           } else {  // packed: every pixel sum stays below 2^16
-            i0a += p01; i0c += p23;
+            i0[0] += p01; i0[1] += p23; i0[2] += q01; i0[3] += q23;
           }
         }
         off += slice_bytes;
@@ -227,12 +270,10 @@ __device__ __forceinline__ void project_volume(const BTask& t, uint32_t* sm, uin
       }
       const int b0 = o[0] + y * L + x0;  // (y, x)
       if constexpr (WIDE) {
-        atomicAdd(sm + b0, i0a);
-        atomicAdd(sm + b0 + 1, i0b);
-        atomicAdd(sm + b0 + 2, i0c);
-        atomicAdd(sm + b0 + 3, i0d);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) atomicAdd(sm + b0 + i, i0[i]);
       } else {
-        add4<false>(sm, b0, i0a, i0c);
+        add8<false>(sm, b0, i0[0], i0[1], i0[2], i0[3]);
       }
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -775,7 +816,7 @@ void classify(const dpma_volume_desc* descs, int count, Classified* c) {
         // counting two loads of overhead per work item
         const int64_t slice_bytes = d.L * d.M * (int64_t)(d.dtype == DPMA_U8 ? 1 : 2);
         const int64_t G = stage_slices(slice_bytes, (int)d.N);
-        const int64_t npos = d.M * ((d.L + 3) / 4);
+        const int64_t npos = d.M * ((d.L + kChunk - 1) / kChunk);
         for (int v = 0; v < 2; ++v) {
           const int64_t nt = v ? 512 : 256;
           int64_t best = -1, bz = 1;
