@@ -194,6 +194,25 @@ def test_footprint_split_matches_single_volume(dpma):
         assert g == single(dpma, t, 3, d)
 
 
+def test_two_cta_launch_every_order(dpma):
+    """Small volumes only: one fused launch of 256-thread CTAs, two per SM,
+    through every order 0..8, 16- and 32-bit pixels, int64 and int128 row
+    sums (the (4, 8, 40) u16 volume at K = 8 needs int128)."""
+    cases = [((4, 8, 40), np.uint16, 8), ((6, 10, 12), np.uint16, 8), ((5, 7, 9), np.uint8, 7),
+             ((3, 30, 20), np.uint16, 6), ((8, 8, 8), np.uint8, 5), ((2, 3, 50), np.uint16, 4),
+             ((7, 5, 3), np.uint8, 3), ((1, 1, 1), np.uint16, 0), ((2, 2, 2), np.uint8, 1),
+             ((3, 4, 5), np.uint16, 2), ((9, 13, 17), np.uint8, 8)]
+    tv = [dev(synth.uniform_volume(sh, dt, seed=300 + i)) for i, (sh, dt, _) in enumerate(cases)]
+    Ks = [K for _, _, K in cases]
+    b = dpma.Batch([t for t, _ in tv], Ks, [d for _, d in tv])
+    assert b.info(0) == len(tv) and b.info(5) == 1 and b.info(2) == 256
+    out = b.out_buffer()
+    b.run(out)
+    b.status()
+    for (t, d), K, g in zip(tv, Ks, b.values(out)):
+        assert g == single(dpma, t, K, d), (tuple(t.shape), K)
+
+
 def test_batch_rejects_bad_descriptors(dpma):
     t, d = dev(synth.uniform_volume((4, 4, 4), np.uint8, seed=1))
     with pytest.raises(dpma.DpmaError) as e:
