@@ -48,6 +48,9 @@ namespace {
 // the 2-D moments T_ab of every image of the volume being reduced (int128)
 constexpr int kPartBytes = kMaxImages * kMax2D * 16;
 constexpr int kSlabWords = 6144;  // one stage buffer (24 KB), double-buffered
+// stage buffers of a one-CTA-per-SM launch whose images leave room (48 KB):
+// half as many stages, so half as many stage barriers
+constexpr int kSlabWordsBig = 12288;
 constexpr int kChunk = 8;  // voxels of one row per projection position
 // words past the last image: the zero adds of a ragged chunk reach up to
 // kChunk - 1 pixels past a row
@@ -62,7 +65,14 @@ struct FusedParams {
   int ntasks;
   int* counter;      // work queue head (zeroed before each run)
   i128* T;           // 2-D moments of every volume
+  int slab_words;    // words of one stage buffer: kSlabWords or kSlabWordsBig
 };
+
+// Which of a task's z-block choices a launch uses: 256 threads, or 512
+// threads with standard or big stage buffers.
+__host__ __device__ __forceinline__ int zblock_index(int nt, int sw) {
+  return nt == 256 ? 0 : (sw == kSlabWordsBig ? 2 : 1);
+}
 
 // ---------------------------------------------------------------- pixels
 
@@ -135,8 +145,8 @@ __device__ __forceinline__ void add8(uint32_t* sm, int b, uint32_t p01, uint32_t
 // Slices per projection stage: as many as fit in one buffer with the 16-byte
 // alignment head and the bytes a chunk load may read past the stage (the
 // aligned words covering a chunk: up to 18 bytes past its last voxel).
-__host__ __device__ __forceinline__ int stage_slices(int64_t slice_bytes, int N) {
-  const int64_t g = ((int64_t)(kSlabWords - 8) * 4 - 30) / slice_bytes;
+__host__ __device__ __forceinline__ int stage_slices(int64_t slice_bytes, int N, int sw) {
+  const int64_t g = ((int64_t)(sw - 8) * 4 - 30) / slice_bytes;
   return (int)(g < 1 ? 1 : (g < N ? g : N));
 }
 
@@ -144,10 +154,10 @@ __host__ __device__ __forceinline__ int stage_slices(int64_t slice_bytes, int N)
 // stage buffer dst (cp.async, 16-byte blocks, one commit group); returns the
 // byte offset of slice z0 in the buffer.
 template <int NT>
-__device__ __forceinline__ int fetch_stage(const BTask& t, int z0, uint32_t* dst) {
+__device__ __forceinline__ int fetch_stage(const BTask& t, int z0, uint32_t* dst, int sw) {
   const int esize = t.dtype == DPMA_U8 ? 1 : 2;
   const int slice_bytes = t.L * t.M * esize;
-  const int G = stage_slices(slice_bytes, t.N);
+  const int G = stage_slices(slice_bytes, t.N, sw);
   const uintptr_t a = reinterpret_cast<uintptr_t>(t.vol) + (uintptr_t)z0 * slice_bytes;
   const uintptr_t a16 = a & ~(uintptr_t)15;
   const int hd = (int)(a - a16);
@@ -179,22 +189,22 @@ __device__ __forceinline__ int fetch_stage(const BTask& t, int z0, uint32_t* dst
 // pixel index moves by a constant per z-step.
 template <typename T, bool WIDE, bool MANY, int NT>
 __device__ __forceinline__ void project_volume(const BTask& t, uint32_t* sm, uint32_t* slab,
-                                               const uint32_t* first, int head0) {
+                                               const uint32_t* first, int head0, int sw) {
   const int L = t.L, M = t.M, N = t.N, P = t.P;
   const int F3 = L + N - 1, F7 = L + M - 1;
   const int* o = t.img_off;
   const int slice_bytes = L * M * (int)sizeof(T);
-  const int G = stage_slices(slice_bytes, N);
+  const int G = stage_slices(slice_bytes, N, sw);
   const int nc = (L + kChunk - 1) / kChunk, npos = M * nc;
-  const int Zg = t.zblocks[NT == 512 ? 1 : 0];  // z-blocks per stage
+  const int Zg = t.zblocks[zblock_index(NT, sw)];  // z-blocks per stage
   int head = head0, head_next = 0;
   const uint32_t* cur = first;
   for (int z0 = 0, si = 0; z0 < N; z0 += G, ++si) {
     // in flight while this stage is processed: buffer si & 1 was last read
     // in stage si - 1 (or by the previous volume's moment stage), before a
     // barrier
-    uint32_t* nxt = slab + (si & 1) * kSlabWords;
-    if (z0 + G < N) head_next = fetch_stage<NT>(t, z0 + G, nxt);
+    uint32_t* nxt = slab + (si & 1) * sw;
+    if (z0 + G < N) head_next = fetch_stage<NT>(t, z0 + G, nxt, sw);
     const unsigned char* S = reinterpret_cast<const unsigned char*>(cur);
     const int gz = min(G, N - z0), zlen = (gz + Zg - 1) / Zg;
     for (int it = threadIdx.x; it < npos * Zg; it += NT) {
@@ -545,9 +555,9 @@ __device__ __forceinline__ void volume_moments(const BTask& t, const uint32_t* s
 
 template <typename T, bool WIDE, int NT>
 __device__ __forceinline__ void project_any(const BTask& t, uint32_t* sm, uint32_t* slab,
-                                            const uint32_t* first, int head0) {
-  if (t.P > 5) project_volume<T, WIDE, true, NT>(t, sm, slab, first, head0);
-  else project_volume<T, WIDE, false, NT>(t, sm, slab, first, head0);
+                                            const uint32_t* first, int head0, int sw) {
+  if (t.P > 5) project_volume<T, WIDE, true, NT>(t, sm, slab, first, head0, sw);
+  else project_volume<T, WIDE, false, NT>(t, sm, slab, first, head0, sw);
 }
 
 template <bool WIDE, int NT>
@@ -563,16 +573,17 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) batch_fused_kernel(Fuse
   extern __shared__ __align__(16) unsigned char smem_raw[];
   i128* Tacc = reinterpret_cast<i128*>(smem_raw);
   __shared__ ImgMeta meta[kMaxImages + 1];
-  uint32_t* slab = reinterpret_cast<uint32_t*>(smem_raw + kPartBytes);  // [2][kSlabWords]
+  const int sw = p.slab_words;
+  uint32_t* slab = reinterpret_cast<uint32_t*>(smem_raw + kPartBytes);  // [2][sw]
   // stage buffer 1 receives the next volume's stage 0 while the moment
-  // stage uses buffer 0 as its scratch area
-  uint32_t* pre = slab + kSlabWords;
-  uint32_t* sm = slab + 2 * kSlabWords;  // images
+  // stage uses (the first kSlabWords of) buffer 0 as its scratch area
+  uint32_t* pre = slab + sw;
+  uint32_t* sm = slab + 2 * sw;  // images
   __shared__ int s_first, s_next;
   if (threadIdx.x == 0) s_first = atomicAdd(p.counter, 1);
   __syncthreads();
   int ti = s_first;  // s_first is never written again
-  int head_pre = ti < p.ntasks ? fetch_stage<NT>(p.tasks[p.order[ti]], 0, pre) : 0;
+  int head_pre = ti < p.ntasks ? fetch_stage<NT>(p.tasks[p.order[ti]], 0, pre, sw) : 0;
   while (ti < p.ntasks) {
     const BTask t = p.tasks[p.order[ti]];
     // the next volume is claimed now and its first stage is copied during
@@ -585,14 +596,14 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) batch_fused_kernel(Fuse
     const int next = s_next;
     i128* Tout = p.T + t.t_off;
     if (t.dtype == DPMA_U8) {
-      if (t.wide) project_any<uint8_t, true, NT>(t, sm, slab, pre, head_pre);
-      else project_any<uint8_t, false, NT>(t, sm, slab, pre, head_pre);
+      if (t.wide) project_any<uint8_t, true, NT>(t, sm, slab, pre, head_pre, sw);
+      else project_any<uint8_t, false, NT>(t, sm, slab, pre, head_pre, sw);
     } else {
-      if (t.wide) project_any<uint16_t, true, NT>(t, sm, slab, pre, head_pre);
-      else project_any<uint16_t, false, NT>(t, sm, slab, pre, head_pre);
+      if (t.wide) project_any<uint16_t, true, NT>(t, sm, slab, pre, head_pre, sw);
+      else project_any<uint16_t, false, NT>(t, sm, slab, pre, head_pre, sw);
     }
     // the projection ended with a barrier: `pre` is free
-    if (next < p.ntasks) head_pre = fetch_stage<NT>(p.tasks[p.order[next]], 0, pre);
+    if (next < p.ntasks) head_pre = fetch_stage<NT>(p.tasks[p.order[next]], 0, pre, sw);
     if (t.wide) moments_any<true, NT>(t, sm, slab, Tacc, meta, Tout);
     else moments_any<false, NT>(t, sm, slab, Tacc, meta, Tout);
     __syncthreads();  // s_next, the images and the scratch area are rewritten next
@@ -815,10 +826,10 @@ void classify(const dpma_volume_desc* descs, int count, Classified* c) {
         // z-blocks per stage: the fewest chunk loads on the busiest thread,
         // counting two loads of overhead per work item
         const int64_t slice_bytes = d.L * d.M * (int64_t)(d.dtype == DPMA_U8 ? 1 : 2);
-        const int64_t G = stage_slices(slice_bytes, (int)d.N);
         const int64_t npos = d.M * ((d.L + kChunk - 1) / kChunk);
-        for (int v = 0; v < 2; ++v) {
+        for (int v = 0; v < 3; ++v) {  // the launch shapes of zblock_index
           const int64_t nt = v ? 512 : 256;
+          const int64_t G = stage_slices(slice_bytes, (int)d.N, v == 2 ? kSlabWordsBig : kSlabWords);
           int64_t best = -1, bz = 1;
           for (int64_t zg = 1; zg <= std::min<int64_t>(G, 32); ++zg) {
             const int64_t cost = ((npos * zg + nt - 1) / nt) * ((G + zg - 1) / zg + 2);
@@ -882,8 +893,13 @@ std::vector<int> lpt_order(const std::vector<BTask>& tasks) {
   return order;
 }
 
-size_t fused_smem(size_t max_words) {
-  return (size_t)kPartBytes + 2 * (size_t)kSlabWords * 4 + (max_words + kSlackWords) * 4;
+size_t fused_smem(size_t max_words, int slab_words) {
+  return (size_t)kPartBytes + 2 * (size_t)slab_words * 4 + (max_words + kSlackWords) * 4;
+}
+
+int slab_words_for(size_t max_words, int threads) {
+  return threads == 512 && fused_smem(max_words, kSlabWordsBig) <= (size_t)kSmemLimit ? kSlabWordsBig
+                                                                                        : kSlabWords;
 }
 
 int fused_per_sm(size_t smem, int threads) {
@@ -941,6 +957,7 @@ cudaError_t enqueue_fused(const BTask* d_tasks, const int* d_order, int n, int m
     p.ntasks = G.count;
     p.counter = d_counters + g;
     p.T = d_T;
+    p.slab_words = G.slab_words;
     if (G.threads == 512) {
       e = set_smem<512>(G.smem);
       if (e != cudaSuccess) return e;
@@ -1023,12 +1040,16 @@ void set_split(dpma_batch* b, int X, int nt0) {
   b->ngroups = 0;
   if (X > 0) {
     batch::FusedGroup& g = b->groups[b->ngroups++];
-    g.first = 0; g.count = X; g.smem = batch::fused_smem(w0); g.threads = nt0;
+    g.first = 0; g.count = X; g.threads = nt0;
+    g.slab_words = batch::slab_words_for(w0, nt0);
+    g.smem = batch::fused_smem(w0, g.slab_words);
     g.grid = batch::fused_grid(g.smem, nt0, X);
   }
   if (X < n) {
     batch::FusedGroup& g = b->groups[b->ngroups++];
-    g.first = X; g.count = n - X; g.smem = batch::fused_smem(w1); g.threads = 256;
+    g.first = X; g.count = n - X; g.threads = 256;
+    g.slab_words = batch::slab_words_for(w1, 256);
+    g.smem = batch::fused_smem(w1, g.slab_words);
     g.grid = batch::fused_grid(g.smem, 256, n - X);
   }
 }
@@ -1136,7 +1157,7 @@ dpma_status dpma_batch_create(const dpma_volume_desc* descs, int count, int flag
     std::vector<int> small;
     b->order.clear();
     for (int i : lpt) {
-      if (batch::fused_smem((size_t)tasks[i].words) <= small_limit) small.push_back(i);
+      if (batch::fused_smem((size_t)tasks[i].words, kSlabWords) <= small_limit) small.push_back(i);
       else b->order.push_back(i);
     }
     b->n_over = (int)b->order.size();

@@ -18,7 +18,7 @@ struct BTask {
   int r64;    // 1: row power sums fit int64
   int t64;    // 1: 2-D moments fit int64
   int words;  // 32-bit words of shared memory the images take
-  int zblocks[2];  // z-blocks per projection stage at 256 and 512 threads
+  int zblocks[3];  // z-blocks per projection stage at 256 threads, and at 512 with standard or big stage buffers
   int lseg[2];     // pixels per row segment of the moment stage at 256 and 512 threads
   int img_off[kMaxImages];  // first pixel of each image (even, in pixel units)
   int64_t t_off;            // first 2-D moment of this volume in T (int128 units)
@@ -39,8 +39,12 @@ struct Classified {
 void classify(const dpma_volume_desc* d, int n, Classified* c);
 // Processing order of the fused queue: largest volumes first.
 std::vector<int> lpt_order(const std::vector<BTask>& tasks);
-// Dynamic shared memory of a fused launch whose largest task takes max_words.
-size_t fused_smem(size_t max_words);
+// Dynamic shared memory of a fused launch whose largest task takes max_words
+// and whose two stage buffers hold slab_words words each.
+size_t fused_smem(size_t max_words, int slab_words);
+// Stage-buffer words of a fused launch: big buffers for a 512-thread launch
+// whose images leave room for them, the standard size otherwise.
+int slab_words_for(size_t max_words, int threads);
 // CTAs of a fused launch: resident capacity, at most ntasks.
 int fused_grid(size_t smem, int threads, int ntasks);
 // Resident CTAs per SM of a fused launch.
@@ -57,6 +61,7 @@ struct FusedGroup {
   int first = 0, count = 0;
   size_t smem = 0;
   int threads = 512, grid = 0;
+  int slab_words = 0;
 };
 constexpr int kMaxGroups = 2;
 

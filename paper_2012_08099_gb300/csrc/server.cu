@@ -514,7 +514,8 @@ bool launch_group(dpma_server* s, Group* g, bool fused) {
     if (e == cudaSuccess) {
       batch::FusedGroup grp;
       grp.count = n;
-      grp.smem = batch::fused_smem(c.max_words);
+      grp.slab_words = batch::slab_words_for(c.max_words, 512);
+      grp.smem = batch::fused_smem(c.max_words, grp.slab_words);
       grp.threads = 512;
       grp.grid = batch::fused_grid(grp.smem, 512, n);
       e = batch::enqueue_fused(reinterpret_cast<const BTask*>(cdev),
