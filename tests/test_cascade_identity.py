@@ -8,7 +8,10 @@ to m_k = (-1)^k Q_k, yields sum (D - w)^b I, the power sums in the signed
 coordinate c = f - off_f with D = f_start + n - off_f (Eq. 1 with the
 origin shift of Sec. 5).  The kernel does all of it modulo 2^128; the test
 does the same and compares with the direct sums, and checks that A_0..A_4
-stay below 2^64 for segments of at most 128 pixels of 32-bit values.
+stay below 2^64 for segments of at most 128 pixels of 32-bit values.  The
+batched kernel runs the same cascade over interleaved segments
+(f = g, g + nseg, ...), scaling the Stirling step by (-nseg)^k, modulo 2^64
+when the host's bound says the row power sums fit int64.
 """
 import random
 from math import comb, factorial
@@ -78,3 +81,54 @@ def test_summed_segments_give_the_row():
         tot = [(a + b) % M128 for a, b in zip(tot, Fs)]
     for b in range(K + 1):
         assert tot[b] == sum((f - off_f) ** b * v for f, v in enumerate(row)) % M128
+
+
+def strided_segment_power_sums(I_row, K, g, nseg, off_f, modulus):
+    """The batched kernel's steps for the interleaved segment f = g, g + nseg,
+    ... of one row: the same cascade over its n pixels, then the Stirling
+    conversion scaled by (-nseg)^k (the coordinate is D - nseg w with
+    D = g + nseg n - off_f) and the Pascal recurrence, modulo `modulus`."""
+    pix = I_row[g::nseg]
+    n = len(pix)
+    A = [0] * (K + 1)
+    for v in pix:
+        A[0] = (A[0] + v) % modulus
+        for j in range(1, K + 1):
+            A[j] = (A[j] + A[j - 1]) % modulus
+    m, sc = [], 1
+    for b in range(K + 1):
+        q = sum((-1) ** (b - j) * stirling2(b, j) * factorial(j) * A[j] for j in range(b + 1))
+        m.append(q * sc % modulus)
+        sc = sc * (-nseg) % modulus
+    D = g + nseg * n - off_f
+    for i in range(1, K + 1):
+        for b in range(K, i - 1, -1):
+            m[b] = (m[b] + D * m[b - 1]) % modulus
+    return m
+
+
+def test_interleaved_segments_modulo_2_64():
+    """Interleaved segments (the batched moment stage) computed modulo 2^64
+    give the exact power sums whenever those fit int64, and the nseg
+    segments of a row add up to the row's power sums."""
+    rng = random.Random(23)
+    M64 = 1 << 64
+    for _ in range(150):
+        K = rng.randint(0, 8)
+        F = rng.randint(1, 400)
+        nseg = rng.randint(1, min(F, 24))
+        off_f = rng.randint(0, F)
+        row = [rng.choice([0, rng.randint(0, 65535)]) for _ in range(F)]
+        tot = [0] * (K + 1)
+        for g in range(nseg):
+            Fs = strided_segment_power_sums(row, K, g, nseg, off_f, M64)
+            for b in range(K + 1):
+                direct = sum((f - off_f) ** b * row[f] for f in range(g, F, nseg))
+                if abs(direct) < 2**63:
+                    signed = Fs[b] - M64 if Fs[b] >= 2**63 else Fs[b]
+                    assert signed == direct, (K, F, nseg, g, b)
+                else:
+                    assert Fs[b] == direct % M64
+            tot = [(a + c) % M64 for a, c in zip(tot, Fs)]
+        for b in range(K + 1):
+            assert tot[b] == sum((f - off_f) ** b * v for f, v in enumerate(row)) % M64
