@@ -97,6 +97,22 @@ int dpma_moment_index(int p, int q, int r);
 const char* dpma_status_string(dpma_status s);
 /* Thread-local message describing the calling thread's last failure ("" if none). */
 const char* dpma_last_error(void);
+/*
+ * Which float32 pipeline produced the calling thread's last synchronous
+ * float32 result (dpma_moments, dpma_moments_host): 0 the quantised
+ * integer-lane pipeline; otherwise the compensated float pipeline recomputed
+ * it because bit 0: a voxel lay beyond the sampled quantisation grid or was
+ * not finite, bit 1: a moment's guaranteed error bound exceeded the
+ * tolerance.  Integer volumes leave it 0.
+ */
+int dpma_last_float_path(void);
+/*
+ * Fault-injection hook for tests of the bounded device waits: the number of
+ * clock cycles a wait of the projection kernel spins before it gives up and
+ * the call reports DPMA_ERR_TIMEOUT (0 restores the default, about 2^31).
+ * Copies already issued still land before a CTA leaves.  Process-wide.
+ */
+dpma_status dpma_set_wait_budget(int64_t cycles);
 /* Geometry of image k (0..8) of an L x M x N volume (table above). */
 dpma_status dpma_image_geometry(int k, int64_t L, int64_t M, int64_t N, int64_t* S, int64_t* F,
                                 int64_t* off_s, int64_t* off_f);
@@ -317,7 +333,9 @@ typedef struct dpma_server_config {
   int32_t max_pending;
 } dpma_server_config;
 
-/* Counters since creation (or the last reset); latencies are submit-to-done. */
+/* Counters since creation (or the last reset).  Latencies run from the entry
+ * to dpma_server_submit (before the volume is copied into pinned memory) to
+ * the moment the result is complete on the host. */
 typedef struct dpma_server_counters {
   int64_t submitted, completed, failed, rejected, pending, inflight, launches;
   int64_t device_bytes_peak;
@@ -400,17 +418,26 @@ dpma_status dpma_server_destroy(dpma_server* server);
  *
  * Same result as dpma_moments_async (device `volume` and `out`, enqueued on
  * `stream`, returns once enqueued), but the workspace -- projection images,
- * partial sums, combine tables, status word -- lives in one static device
- * array of 32 MiB (32 MiB - 64 KiB for the workspace) that every GPU which
- * loads the library holds until the process exits; the call allocates no
- * device memory.  Volumes needing more workspace than that (dpma_workspace_size)
- * are refused with DPMA_ERR_REJECTED; 512^3 float32 at K = 6 fits.
+ * partial sums, status word -- lives in one static device array of 32 MiB,
+ * and the combine tables of every order in a second one of 128 KiB; every
+ * GPU which loads the library holds both until the process exits.  The call
+ * allocates no device memory.  Volumes needing more workspace than 32 MiB
+ * (dpma_workspace_size) are refused with DPMA_ERR_REJECTED; 512^3 float32 at
+ * K = 6 fits.
  *
- * The first call on a device (with that device current) looks up the array's
- * device address; make that first call before any stream capture.  Every
- * call reuses the same array and clears what must start at zero; calls whose
- * work overlaps on the GPU race on it and must be serialised by the caller.
- * A combine self-check failure is not reported by this entry point.
+ * The first call on a device (with that device current) looks up the arrays'
+ * device addresses and copies the combine tables into the second array
+ * (synchronously); make that first call before any stream capture.  Later
+ * calls only launch kernels.  Every call reuses the same workspace array and
+ * clears what must start at zero; calls whose work overlaps on the GPU race
+ * on it and must be serialised by the caller.
+ *
+ * A failure on the device (a bounded wait that gave up, DPMA_ERR_TIMEOUT; a
+ * combine division that left a remainder, DPMA_ERR_INTERNAL) cannot be
+ * returned by this asynchronous call; instead every one of the
+ * dpma_num_moments(K) output moments is overwritten with a sentinel: a quiet
+ * NaN for float32 volumes, the most negative int128 (-2^127) for integer
+ * volumes, a value no integer volume's moment can take.
  */
 dpma_status dpma_moments_noalloc(const void* volume, int64_t L, int64_t M, int64_t N,
                                  dpma_dtype dtype, int K, void* out, void* stream);

@@ -84,6 +84,8 @@ def lib():
                 "dpma_moment_index": (ip, [ip, ip, ip]),
                 "dpma_status_string": (ctypes.c_char_p, [ip]),
                 "dpma_last_error": (ctypes.c_char_p, []),
+                "dpma_last_float_path": (ip, []),
+                "dpma_set_wait_budget": (ip, [i64]),
                 "dpma_image_geometry": (ip, [ip, i64, i64, i64, P64, P64, P64, P64]),
                 "dpma_images_size": (sz, [i64, i64, i64, ip, ip]),
                 "dpma_workspace_size": (sz, [i64, i64, i64, ip, ip]),
@@ -133,6 +135,20 @@ def _check(rc: int):
 
 
 # ---------------------------------------------------------------- helpers
+
+
+def last_float_path() -> int:
+    """0 if the calling thread's last synchronous float32 call was served by
+    the quantised integer-lane pipeline; otherwise the flags that sent it to
+    the compensated fallback (1: a voxel beyond the grid, 2: an error bound
+    above the tolerance)."""
+    return lib().dpma_last_float_path()
+
+
+def set_wait_budget(cycles: int):
+    """Test hook: cycles a bounded device wait spins before it gives up (0:
+    the default)."""
+    _check(lib().dpma_set_wait_budget(cycles))
 
 
 def num_moments(K: int) -> int:

@@ -8,6 +8,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -25,6 +27,11 @@ using namespace dpma;
 namespace {
 
 thread_local std::string t_last_error;
+// flags word of the calling thread's last synchronous float32 call: 0 when
+// the quantised pipeline gave the result, 1 / 2 when the compensated
+// fallback recomputed it (a voxel beyond the grid / an error bound above the
+// tolerance)
+thread_local int t_last_flags = 0;
 
 dpma_status fail(dpma_status s, const std::string& msg) {
   t_last_error = msg;
@@ -65,9 +72,13 @@ dpma_status check_args(int64_t L, int64_t M, int64_t N, dpma_dtype dtype, int K)
 struct Layout {
   ImageSet set;
   size_t img_bytes, part_bytes, m2d_bytes;
-  size_t off_img, off_part, off_m2d, off_status, total;
+  size_t off_img, off_part, off_m2d, off_sample, off_status, total;
+  // status block: [0] status, [1] flags, [2] e1, [3] B
 };
 
+// One workspace serves both float32 pipelines: the quantised-limb one (two
+// int32 image sets, int128 partials and moments for 2P images) and its
+// compensated fallback (double images, float-pair partials and moments).
 Layout layout(int64_t L, int64_t M, int64_t N, dpma_dtype dtype, int K) {
   Layout w;
   const bool fl = is_float(dtype);
@@ -75,13 +86,27 @@ Layout layout(int64_t L, int64_t M, int64_t N, dpma_dtype dtype, int K) {
   w.img_bytes = (size_t)w.set.total_elems * (fl ? 8 : 4);
   w.part_bytes = moments2d_partials_bytes(w.set, K, fl);
   w.m2d_bytes = (size_t)w.set.P * num_2d(K) * (fl ? 8 : 16);
+  if (fl) {
+    w.part_bytes = std::max(w.part_bytes, moments2d_partials_bytes_limbs(w.set, K, 2));
+    w.m2d_bytes = std::max(w.m2d_bytes, (size_t)2 * w.set.P * num_2d(K) * 16);
+  }
   w.off_img = 0;
   w.off_part = align_up(w.off_img + w.img_bytes, 256);
   w.off_m2d = align_up(w.off_part + w.part_bytes, 256);
-  w.off_status = align_up(w.off_m2d + w.m2d_bytes, 256);
+  w.off_sample = align_up(w.off_m2d + w.m2d_bytes, 256);
+  w.off_status = align_up(w.off_sample + (fl ? kMaxSample * sizeof(uint32_t) : 0), 256);
   w.total = w.off_status + 256;
   return w;
 }
+
+// Cycles a bounded device wait of the projection may spin (a test hook can
+// shorten it).
+std::atomic<long long> g_wait_budget{1ll << 31};
+
+// Float32 results of the quantised pipeline are guaranteed within this
+// fraction of the moment of |V| (the method's tolerance is 1e-6); a moment
+// whose error bound is larger sends the volume to the compensated fallback.
+constexpr double kFloatTolerance = 1e-7;
 
 // Library-owned per-device resources.
 struct DeviceState {
@@ -101,7 +126,7 @@ struct DeviceState {
 // destination would make every synchronous call pay a staged copy).
 cudaError_t ensure_host_status(DeviceState* s) {
   if (s->h_status) return cudaSuccess;
-  return cudaMallocHost(reinterpret_cast<void**>(&s->h_status), sizeof(int));
+  return cudaMallocHost(reinterpret_cast<void**>(&s->h_status), 2 * sizeof(int));
 }
 
 std::mutex g_states_mu;
@@ -197,11 +222,46 @@ int64_t host_chunk_slices(int64_t N, size_t vbytes) {
   return (N + n - 1) / n;
 }
 
+// The float32 fallback: the compensated float kernels over the whole volume,
+// each launch gated on the flags word, so it costs nothing but its launches
+// unless the quantised pipeline flagged the volume (a voxel beyond the grid,
+// a non-finite voxel, or a moment whose guaranteed error exceeds the
+// tolerance).  Then it overwrites images, moments and `out`.
+dpma_status enqueue_float_fallback(const void* volume, int64_t L, int64_t M, int64_t N, int K,
+                                   void* out, cudaStream_t st, unsigned char* ws, const Layout& w) {
+  int* status = reinterpret_cast<int*>(ws + w.off_status);
+  const int* gate = status + 1;
+  void* images = ws + w.off_img;
+  cudaError_t e = launch_clear(images, w.img_bytes, nullptr, st, gate);
+  if (e != cudaSuccess) return cuda_fail(e, "clear images (fallback)");
+  ProjectArgs a{};
+  a.vol = volume;
+  a.L = L; a.M = M; a.N = N;
+  a.dtype = (int)DPMA_F32;
+  a.K = K;
+  a.images = images;
+  a.set = w.set;
+  a.status = status;
+  a.gate = gate;
+  e = launch_project(a, st);
+  if (e != cudaSuccess) return cuda_fail(e, "projection kernel (fallback)");
+  e = launch_image_moments(images, w.set, K, true, ws + w.off_part, ws + w.off_m2d, st, gate);
+  if (e != cudaSuccess) return cuda_fail(e, "image moment kernel (fallback)");
+  e = launch_combine(ws + w.off_m2d, K, true, out, status, st, gate);
+  if (e != cudaSuccess) return cuda_fail(e, "combine kernel (fallback)");
+  return DPMA_OK;
+}
+
 // The pipeline on stream st.  With a host source (host_src non-null) the
 // volume is copied into `volume` in z-chunks on copy_st, and the projection
 // of each chunk starts as soon as its copy has landed, so the copy of the
 // next chunk overlaps it; launches over disjoint z-ranges add up to the
 // images of the whole volume.
+//
+// Volumes with 16-byte aligned rows and at most 7 images take the
+// integer-lane projection (exact integer images; float32 volumes as two
+// quantisation limbs, with the gated compensated fallback behind them); the
+// others take the compensated/integer projection of k1_project.cuh.
 dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dtype dtype, int K,
                     void* out, cudaStream_t st, unsigned char* ws, const Layout& w,
                     const void* host_src = nullptr, cudaStream_t copy_st = nullptr,
@@ -209,8 +269,26 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
   cudaError_t e = prepare_combine(K);
   if (e != cudaSuccess) return cuda_fail(e, "combine plan");
   StageRecorder rec(st);
+  const bool fl = is_float(dtype);
   void* images = ws + w.off_img;
-  e = launch_clear(images, w.img_bytes, reinterpret_cast<int*>(ws + w.off_status), st);
+  int* status = reinterpret_cast<int*>(ws + w.off_status);
+  int* flags = status + 1;
+  int* scale = status + 2;
+  uint32_t* sample = reinterpret_cast<uint32_t*>(ws + w.off_sample);
+  const int B = fl ? float_limb_bits(L, M, N, K) : 0;
+  const bool lanes = project_int_supported(volume, L, (int)dtype, w.set.P) &&
+                     (!fl || B >= kMinLimbBits);
+  int ia_nsample = 0;
+  if (!lanes) {
+    e = launch_clear(images, w.img_bytes, status, st);
+  } else {
+    // the images (rounded up to 16 bytes: the padding before the next
+    // section), the status words and, for a device-resident float volume,
+    // the magnitude sample
+    e = launch_clear_sample(images, align_up(w.img_bytes, 16), status, flags,
+                            fl && !host_src ? static_cast<const float*>(volume) : nullptr, L, M,
+                            0, N, fl && !host_src ? sample : nullptr, &ia_nsample, st);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "clear images");
   rec.mark(0);
   ProjectArgs a{};
@@ -220,10 +298,24 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
   a.K = K;
   a.images = images;
   a.set = w.set;
-  a.status = reinterpret_cast<int*>(ws + w.off_status);
+  a.status = status;
+  IntProjectArgs ia{};
+  ia.vol = volume;
+  ia.L = L; ia.M = M; ia.N = N;
+  ia.dtype = (int)dtype;
+  ia.images = images;
+  ia.set = w.set;
+  ia.status = status;
+  ia.flags = flags;
+  ia.sample = fl ? sample : nullptr;
+  ia.limb_bits = B;
+  ia.scale_out = fl ? scale : nullptr;
+  ia.wait_budget = g_wait_budget.load();
+  ia.nsample = ia_nsample;
   if (host_src) {
     const size_t slice = (size_t)L * M * elem_size(dtype);
-    const int64_t zc = host_chunk_slices(N, slice * N);
+    int64_t zc = host_chunk_slices(N, slice * N);
+    zc += zc & 1;  // even chunks: the integer-lane projection takes z-pairs
     // the staging buffer is rewritten only after all earlier work on st
     e = cudaEventRecord(ev, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(copy_st, ev, 0);
@@ -235,22 +327,49 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
       if (e == cudaSuccess) e = cudaEventRecord(ev, copy_st);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
       if (e != cudaSuccess) return cuda_fail(e, "copy volume chunk to device");
-      a.z0 = z0;
-      a.nz = nz;
-      e = launch_project(a, st);
+      if (lanes && fl && z0 == 0) {
+        // the quantisation grid from the first chunk (8x headroom; a later
+        // voxel beyond it raises the fallback)
+        e = launch_clear_sample(images, 0, nullptr, nullptr, static_cast<const float*>(volume),
+                                L, M, 0, nz, sample, &ia.nsample, st);
+        if (e != cudaSuccess) return cuda_fail(e, "magnitude sample");
+      }
+      if (lanes) {
+        ia.z0 = z0;
+        ia.nz = nz;
+        e = launch_project_int(ia, st);
+      } else {
+        a.z0 = z0;
+        a.nz = nz;
+        e = launch_project(a, st);
+      }
       if (e != cudaSuccess) return cuda_fail(e, "projection kernel");
     }
     if (e != cudaSuccess) return cuda_fail(e, "copy volume to device");
   } else {
-    e = launch_project(a, st);
+    if (lanes) {
+      e = launch_project_int(ia, st);
+    } else {
+      e = launch_project(a, st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "projection kernel");
   }
   rec.mark(1);
-  const bool fl = is_float(dtype);
+  if (lanes && fl) {
+    e = launch_image_moments_limbs(images, w.set, w.set.total_elems, K, 2, ws + w.off_part,
+                                   ws + w.off_m2d, st);
+    if (e != cudaSuccess) return cuda_fail(e, "image moment kernel");
+    rec.mark(2);
+    e = launch_combine_fixed(ws + w.off_m2d, K, w.set.P, static_cast<double*>(out), status, flags,
+                             scale, L, M, N, kFloatTolerance, st);
+    if (e != cudaSuccess) return cuda_fail(e, "combine kernel");
+    rec.mark(3);
+    return enqueue_float_fallback(volume, L, M, N, K, out, st, ws, w);
+  }
   e = launch_image_moments(images, w.set, K, fl, ws + w.off_part, ws + w.off_m2d, st);
   if (e != cudaSuccess) return cuda_fail(e, "image moment kernel");
   rec.mark(2);
-  e = launch_combine(ws + w.off_m2d, K, fl, out, reinterpret_cast<int*>(ws + w.off_status), st);
+  e = launch_combine(ws + w.off_m2d, K, fl, out, status, st);
   if (e != cudaSuccess) return cuda_fail(e, "combine kernel");
   rec.mark(3);
   return DPMA_OK;
@@ -290,6 +409,14 @@ const char* dpma_status_string(dpma_status s) {
 }
 
 const char* dpma_last_error(void) { return t_last_error.c_str(); }
+
+int dpma_last_float_path(void) { return t_last_flags; }
+
+dpma_status dpma_set_wait_budget(int64_t cycles) {
+  if (cycles < 0) return fail(DPMA_ERR_INVALID_ARG, "negative wait budget");
+  g_wait_budget.store(cycles == 0 ? (1ll << 31) : cycles);
+  return DPMA_OK;
+}
 
 dpma_status dpma_image_geometry(int k, int64_t L, int64_t M, int64_t N, int64_t* S, int64_t* F,
                                 int64_t* off_s, int64_t* off_f) {
@@ -369,10 +496,11 @@ dpma_status dpma_moments(const void* volume, int64_t L, int64_t M, int64_t N, dp
   if (e != cudaSuccess) return cuda_fail(e, "pinned status word");
   s = enqueue(volume, L, M, N, dtype, K, out, ds->stream, ws, w);
   if (s != DPMA_OK) return s;
-  e = cudaMemcpyAsync(ds->h_status, ws + w.off_status, sizeof(int), cudaMemcpyDeviceToHost,
+  e = cudaMemcpyAsync(ds->h_status, ws + w.off_status, 2 * sizeof(int), cudaMemcpyDeviceToHost,
                       ds->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ds->stream);
   if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+  t_last_flags = ds->h_status[1];
   const int status = *ds->h_status;
   if (status == DPMA_ERR_TIMEOUT) return fail(DPMA_ERR_TIMEOUT, "a bounded device wait gave up");
   if (status) return fail(DPMA_ERR_INTERNAL, "combine division left a remainder");
@@ -416,10 +544,11 @@ dpma_status dpma_moments_host(const void* host_volume, int64_t L, int64_t M, int
   if (e != cudaSuccess) return cuda_fail(e, "pinned status word");
   e = cudaMemcpyAsync(host_out, ds->host_out, out_bytes, cudaMemcpyDeviceToHost, ds->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(ds->h_status, ws + w.off_status, sizeof(int), cudaMemcpyDeviceToHost,
+    e = cudaMemcpyAsync(ds->h_status, ws + w.off_status, 2 * sizeof(int), cudaMemcpyDeviceToHost,
                         ds->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ds->stream);
   if (e != cudaSuccess) return cuda_fail(e, "copy moments to host");
+  t_last_flags = ds->h_status[1];
   const int status = *ds->h_status;
   if (status == DPMA_ERR_TIMEOUT) return fail(DPMA_ERR_TIMEOUT, "a bounded device wait gave up");
   if (status) return fail(DPMA_ERR_INTERNAL, "combine division left a remainder");
@@ -435,6 +564,19 @@ dpma_status dpma_project(const void* volume, int64_t L, int64_t M, int64_t N, dp
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(images, 0, w.img_bytes, st);
   if (e != cudaSuccess) return cuda_fail(e, "clear images");
+  if (!is_float(dtype) && project_int_supported(volume, L, (int)dtype, w.set.P)) {
+    // integer volumes: the integer-lane kernel of the fused pipeline
+    IntProjectArgs ia{};
+    ia.vol = volume;
+    ia.L = L; ia.M = M; ia.N = N;
+    ia.dtype = (int)dtype;
+    ia.images = images;
+    ia.set = w.set;
+    ia.wait_budget = g_wait_budget.load();
+    e = launch_project_int(ia, st);
+    if (e != cudaSuccess) return cuda_fail(e, "projection kernel");
+    return DPMA_OK;
+  }
   ProjectArgs a{};
   a.vol = volume;
   a.L = L; a.M = M; a.N = N;

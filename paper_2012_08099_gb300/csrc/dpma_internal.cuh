@@ -97,24 +97,79 @@ struct ProjectArgs {
   // slices z0 .. z0 + nz - 1 only (nz = 0: the whole volume); the images
   // are accumulated, so launches over disjoint ranges add up to the volume
   int64_t z0 = 0, nz = 0;
+  // fallback launches: the kernel does nothing unless (*gate & 3) != 0
+  const int* gate = nullptr;
 };
 
 // Zeroes `bytes` (a multiple of 4) at `p` and, if non-null, the status word,
 // in one launch: 16-byte stores when p is 16-byte aligned, 4-byte stores for
 // the tail.  Falls back to cudaMemsetAsync for a misaligned p.
-cudaError_t launch_clear(void* p, size_t bytes, int* status, cudaStream_t st);
+cudaError_t launch_clear(void* p, size_t bytes, int* status, cudaStream_t st,
+                         const int* gate = nullptr);
 
 // Step 1: images must be zeroed by the caller (the launcher does not clear).
 cudaError_t launch_project(const ProjectArgs& a, cudaStream_t st);
+
+// Step 1 on integer lanes (k1_int.cuh): uint32 images for integer volumes;
+// for float32 volumes two sets of int32 images, one per quantisation limb
+// (limb l of image k at base[k] + l * set.total_elems).
+struct IntProjectArgs {
+  const void* vol;
+  int64_t L, M, N;
+  int dtype;  // 0 u8, 1 u16, 2 f32
+  void* images;
+  ImageSet set;
+  int* status;               // bounded-wait timeouts (may be null)
+  int* flags;                // float volumes: |= 1 when a voxel leaves the grid
+  const uint32_t* sample;    // float volumes: sampled |v| maxima (float bits)
+  int nsample;
+  int limb_bits;             // float volumes: B, |limb| <= 2^B
+  int* scale_out;            // float volumes: receives e1 (may be null)
+  long long wait_budget;     // cycles a bounded wait may spin
+  int64_t z0 = 0, nz = 0;    // slices z0 .. z0 + nz - 1 (nz = 0: all; nz even unless it ends at N)
+};
+// Whether the integer-lane kernel takes this volume (16-byte aligned rows
+// and at most 7 images).
+bool project_int_supported(const void* vol, int64_t L, int dtype, int P);
+cudaError_t launch_project_int(const IntProjectArgs& a, cudaStream_t st);
+// Zeroes `bytes` at p (16-byte aligned, a multiple of 16), the status and
+// flags words, and for float volumes (sample != null) writes into
+// sample[0 .. nsample) the maxima of |v| over a sample of rows of slices
+// z0 .. z0 + nz - 1.  Returns the sample length through *nsample.
+cudaError_t launch_clear_sample(void* p, size_t bytes, int* status, int* flags, const float* vol,
+                                int64_t L, int64_t M, int64_t z0, int64_t nz, uint32_t* sample,
+                                int* nsample, cudaStream_t st);
+constexpr int kMaxSample = 2048;  // sample slots
 
 // Step 2: block partials of every image's 2-D moments into `partials`
 // (int128 or float pairs), then a reduction into `m2d`.
 size_t moments2d_partials_bytes(const ImageSet& set, int K, bool is_float);
 cudaError_t launch_image_moments(const void* images, const ImageSet& set, int K, bool is_float,
-                                 void* partials, void* m2d, cudaStream_t st);
+                                 void* partials, void* m2d, cudaStream_t st,
+                                 const int* gate = nullptr);
+// Step 2 on nl limb sets of int32 images (image i of the nl * P is image
+// i % P of limb i / P, at base[i % P] + (i / P) * limb_stride); `m2d`
+// receives nl * P rows of int128 moments.
+constexpr int kMaxLimbImages = 2 * kMaxImages;
+size_t moments2d_partials_bytes_limbs(const ImageSet& set, int K, int nl);
+cudaError_t launch_image_moments_limbs(const void* images, const ImageSet& set, int64_t limb_stride,
+                                       int K, int nl, void* partials, void* m2d, cudaStream_t st);
 
 // Step 3: combine into 3-D moments.
 cudaError_t launch_combine(const void* m2d, int K, bool is_float, void* out, int* status,
-                           cudaStream_t st);
+                           cudaStream_t st, const int* gate = nullptr);
+// Step 3 for the limb images of a float volume: exact combine of both limbs,
+// the join of the limbs, the conversion to double and the guaranteed-error
+// check (flags |= 2 when the quantisation error bound exceeds tol of a moment).
+// scale[0] = e1 and scale[1] = B as the projection stored them.
+cudaError_t launch_combine_fixed(const void* m2d, int K, int P, double* out, int* status,
+                                 int* flags, const int* scale, int64_t L, int64_t M, int64_t N,
+                                 double tol, cudaStream_t st);
+
+// Bits B of the quantisation limbs of a float32 volume (|limb| <= 2^B):
+// every line sum fits in int32 and every limb moment in int128; below
+// kMinLimbBits the float volume takes the compensated float kernel.
+int float_limb_bits(int64_t L, int64_t M, int64_t N, int K);
+constexpr int kMinLimbBits = 12;
 
 }  // namespace dpma

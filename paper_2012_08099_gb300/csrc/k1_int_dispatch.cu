@@ -1,0 +1,125 @@
+// Step 1 on integer lanes: dispatch by element type and image count, the
+// tensor-map encoder, and the kernel that clears the images and samples a
+// float volume's magnitude for the quantisation grid.
+#include <mutex>
+
+#include "k1_int.cuh"
+
+namespace dpma {
+namespace k1i {
+
+EncodeTiledFn encode_tiled_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+cudaError_t launch_u8(int P, const IntProjectArgs& a, cudaStream_t st);
+cudaError_t launch_u16(int P, const IntProjectArgs& a, cudaStream_t st);
+cudaError_t launch_f32(int P, const IntProjectArgs& a, cudaStream_t st);
+
+namespace {
+
+// Grid-stride zeroing with 16-byte stores; block b also takes sampled rows
+// b, b + G, ... of the float volume (row j of the sample is volume row
+// j * rows / nsr, jittered inside its stride) and stores the largest |v|
+// it saw (float bits; NaN propagates) in sample[b].
+__global__ void clear_sample_kernel(uint4* p, int64_t n16, int* status, int* flags,
+                                    const float* vol, int64_t L, int64_t M, int64_t z0,
+                                    int64_t nz, uint32_t* sample, int64_t nsr) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (gid == 0) {
+    if (status) *status = 0;
+    if (flags) *flags = 0;
+  }
+  for (int64_t i = gid; i < n16; i += stride) p[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (!sample) return;
+  const int64_t rows = M * nz;
+  const int64_t step = rows / nsr;  // >= 1
+  float m = 0.f;
+  for (int64_t j = blockIdx.x; j < nsr; j += gridDim.x) {
+    const int64_t row = j * rows / nsr + (step > 1 ? (j * 7919) % step : 0);
+    const int64_t y = row % M, z = z0 + row / M;
+    const float* src = vol + (z * M + y) * L;
+    for (int64_t x = threadIdx.x; x < L; x += blockDim.x) {
+      float d;
+      asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(m), "f"(fabsf(__ldcs(src + x))));
+      m = d;
+    }
+  }
+  __shared__ float red[32];
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    float d;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(m), "f"(__shfl_xor_sync(0xffffffffu, m, o)));
+    m = d;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      float d;
+      asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(m), "f"(red[w]));
+      m = d;
+    }
+    sample[blockIdx.x] = __float_as_uint(m);
+  }
+}
+
+}  // namespace
+}  // namespace k1i
+
+bool project_int_supported(const void* vol, int64_t L, int dtype, int P) {
+  const int64_t es = dtype == 0 ? 1 : (dtype == 1 ? 2 : 4);
+  return P >= 3 && P <= 7 && (L * es) % 16 == 0 && (reinterpret_cast<uintptr_t>(vol) % 16) == 0;
+}
+
+cudaError_t launch_project_int(const IntProjectArgs& a, cudaStream_t st) {
+  const int P = a.set.P;
+  if (!project_int_supported(a.vol, a.L, a.dtype, P)) return cudaErrorInvalidValue;
+  switch (a.dtype) {
+    case 0: return k1i::launch_u8(P, a, st);
+    case 1: return k1i::launch_u16(P, a, st);
+    case 2: return k1i::launch_f32(P, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_clear_sample(void* p, size_t bytes, int* status, int* flags, const float* vol,
+                                int64_t L, int64_t M, int64_t z0, int64_t nz, uint32_t* sample,
+                                int* nsample, cudaStream_t st) {
+  if ((reinterpret_cast<uintptr_t>(p) & 15) != 0 || (bytes & 15) != 0) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int64_t n16 = (int64_t)(bytes / 16);
+  int64_t blocks = (n16 + 255) / 256;
+  const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * 8;
+  if (blocks > cap) blocks = cap;
+  int64_t nsr = 0;
+  if (sample) {
+    // about 4096 sampled rows (every row of a small volume)
+    const int64_t rows = M * nz;
+    nsr = rows < 4096 ? rows : 4096;
+    if (blocks < 64) blocks = 64;
+    if (blocks > kMaxSample) blocks = kMaxSample;
+    if (blocks > nsr) blocks = nsr;
+  }
+  if (blocks < 1) blocks = 1;
+  if (nsample) *nsample = sample ? (int)blocks : 0;
+  k1i::clear_sample_kernel<<<(unsigned)blocks, 256, 0, st>>>(
+      static_cast<uint4*>(p), n16, status, flags, vol, L, M, z0, nz, sample, nsr);
+  return cudaGetLastError();
+}
+
+}  // namespace dpma

@@ -90,6 +90,9 @@ struct K1Params {
   ImageSet set;
   void* images;
   int* status;
+  // when non-null the launch is a fallback: it does nothing unless
+  // (*gate & 3) != 0 (the integer-lane projection flagged the volume)
+  const int* gate;
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -329,6 +332,7 @@ template <int BY> struct ExitLayout {
 template <typename T, int P, bool TMA>
 __global__ void __launch_bounds__(NT, TileCfg<T, P>::MINB)
     k1_project_kernel(K1Params p, const __grid_constant__ CUtensorMap vmap) {
+  if (p.gate && (*p.gate & 3) == 0) return;
   using C = TileCfg<T, P>;
   constexpr bool FL = C::FL;
   using A = typename std::conditional<FL, float, uint32_t>::type;    // accumulators
@@ -1140,6 +1144,7 @@ cudaError_t launch_t(const ProjectArgs& a, cudaStream_t st) {
   p.set = a.set;
   p.images = a.images;
   p.status = a.status;
+  p.gate = a.gate;
 
   auto rnd = [](size_t b) { return (b + 127) & ~size_t(127); };
   using X = ExitLayout<BY>;

@@ -26,11 +26,13 @@ namespace {
 struct K2Params {
   const void* images;
   ImageSet set;
+  int nimg;     // images to reduce: nl * P (image i is image i % P of limb i / P)
   int K;
   int npairs;
   int seg_len;  // integer images: pixels per row segment
-  int64_t blk_base[kMaxImages + 1];  // first block of each image; [P] = total
-  void* partials;                    // [block][npairs] int128 or float2
+  int64_t blk_base[kMaxLimbImages + 1];  // first block of each image; [nimg] = total
+  void* partials;                        // [block][npairs] int128 or float2
+  const int* gate;                       // fallback launch: nothing unless (*gate & 3)
 };
 
 // Integer images by cascaded sums -------------------------------------------
@@ -51,19 +53,23 @@ constexpr int kUnitThreads = 128;  // segments per CTA
 
 __constant__ StirlingTable c_stirling = make_stirling();
 
-template <int K>
+// SGN: the pixels are two's complement int32 (the limb images of a float
+// volume) instead of uint32.
+template <int K, bool SGN>
 __global__ void __launch_bounds__(kUnitThreads) k2_int_cascade_kernel(K2Params p) {
   constexpr int NB = K + 1;
   constexpr int CH = kUnitThreads / NB;  // unit chunks per power b in the fold
   const int blk = blockIdx.x;
-  int k = 0;
-  while (k + 1 < p.set.P && blk >= p.blk_base[k + 1]) ++k;
-  const int64_t chunk = blk - p.blk_base[k];
+  int kk = 0;
+  while (kk + 1 < p.nimg && blk >= p.blk_base[kk + 1]) ++kk;
+  const int k = kk % p.set.P, limb = kk / p.set.P;
+  const int64_t chunk = blk - p.blk_base[kk];
   const int64_t S = p.set.S[k], F = p.set.F[k];
   const int64_t off_s = p.set.off_s[k], off_f = p.set.off_f[k];
   const int64_t seg = p.seg_len;
   const int64_t nseg = (F + seg - 1) / seg;
-  const uint32_t* img = static_cast<const uint32_t*>(p.images) + p.set.base[k];
+  const uint32_t* img =
+      static_cast<const uint32_t*>(p.images) + p.set.base[k] + limb * p.set.total_elems;
   const int t = threadIdx.x;
 
   __shared__ u128 Fs[kUnitThreads][NB];  // row power sums of each segment
@@ -89,18 +95,20 @@ __global__ void __launch_bounds__(kUnitThreads) k2_int_cascade_kernel(K2Params p
 #pragma unroll
     for (int j = 0; j < (NB > 5 ? NB - 5 : 1); ++j) a128[j] = 0;
     for (int i = 0; i < n; ++i) {
-      a64[0] += __ldg(row + i);
+      const uint32_t px = __ldg(row + i);
+      a64[0] += SGN ? (uint64_t)(int64_t)(int32_t)px : (uint64_t)px;
 #pragma unroll
       for (int j = 1; j < N64; ++j) a64[j] += a64[j - 1];
       if constexpr (NB > 5) {
-        a128[0] += a64[4];
+        a128[0] += (u128)(i128)(int64_t)a64[4];
 #pragma unroll
         for (int j = 1; j < NB - 5; ++j) a128[j] += a128[j - 1];
       }
     }
     u128 A[NB];
 #pragma unroll
-    for (int j = 0; j < NB; ++j) A[j] = j < 5 ? (u128)a64[j < 5 ? j : 0] : a128[j >= 5 ? j - 5 : 0];
+    for (int j = 0; j < NB; ++j)
+      A[j] = j < 5 ? (u128)(i128)(int64_t)a64[j < 5 ? j : 0] : a128[j >= 5 ? j - 5 : 0];
     // Q_b = sum_j (-1)^(b-j) S(b,j) j! A_j, then the shift to c = D - w:
     // with m_k = (-1)^k Q_k, F_b = sum_k C(b,k) D^(b-k) m_k, built by the
     // Pascal recurrence m_b += D m_(b-1) applied K times
@@ -219,11 +227,12 @@ __device__ __forceinline__ void ff_mul_f(float hi, float lo, float c, float& rh,
 // row in float-float and folds s^a F_b.
 template <int K>
 __global__ void __launch_bounds__(kUnitThreads) k2_f32_seg_kernel(K2Params p) {
+  if (p.gate && (*p.gate & 3) == 0) return;
   constexpr int NB = K + 1;
   constexpr int CH = kUnitThreads / NB;
   const int blk = blockIdx.x;
   int k = 0;
-  while (k + 1 < p.set.P && blk >= p.blk_base[k + 1]) ++k;
+  while (k + 1 < p.nimg && blk >= p.blk_base[k + 1]) ++k;
   const int64_t chunk = blk - p.blk_base[k];
   const int64_t S = p.set.S[k], F = p.set.F[k];
   const int64_t off_s = p.set.off_s[k], off_f = p.set.off_f[k];
@@ -325,46 +334,56 @@ int int_seg_len(const ImageSet& set) {
   return seg;
 }
 
-// CTAs of step 2 per image: kUnitThreads row segments per CTA.
-int64_t blocks_of(const ImageSet& set, bool is_float, int64_t* base) {
-  (void)is_float;  // both element types use the same segments
+// CTAs of step 2 per image: kUnitThreads row segments per CTA; nl limb sets
+// of the P images (image i is image i % P of limb i / P).
+int64_t blocks_of(const ImageSet& set, int nl, int64_t* base) {
   const int64_t seg = int_seg_len(set);
   int64_t at = 0;
-  for (int k = 0; k < set.P; ++k) {
-    if (base) base[k] = at;
+  for (int i = 0; i < nl * set.P; ++i) {
+    const int k = i % set.P;
+    if (base) base[i] = at;
     const int64_t units = set.S[k] * ((set.F[k] + seg - 1) / seg);
     at += (units + kUnitThreads - 1) / kUnitThreads;
   }
-  if (base) base[set.P] = at;
+  if (base) base[nl * set.P] = at;
   return at;
 }
 
 }  // namespace
 
 size_t moments2d_partials_bytes(const ImageSet& set, int K, bool is_float) {
-  return (size_t)blocks_of(set, is_float, nullptr) * num_2d(K) *
+  return (size_t)blocks_of(set, 1, nullptr) * num_2d(K) *
          (is_float ? sizeof(float2) : sizeof(i128));
 }
 
-// defined in k3_combine.cu: sums the block partials into per-image moments
-cudaError_t launch_reduce_partials(const void* partials, const int64_t* blk_base, int P, int K,
-                                   bool is_float, void* m2d, cudaStream_t st);
+size_t moments2d_partials_bytes_limbs(const ImageSet& set, int K, int nl) {
+  return (size_t)blocks_of(set, nl, nullptr) * num_2d(K) * sizeof(i128);
+}
 
-cudaError_t launch_image_moments(const void* images, const ImageSet& set, int K, bool is_float,
-                                 void* partials, void* m2d, cudaStream_t st) {
+// defined in k3_combine.cu: sums the block partials into per-image moments
+cudaError_t launch_reduce_partials(const void* partials, const int64_t* blk_base, int nimg, int K,
+                                   bool is_float, void* m2d, cudaStream_t st, const int* gate);
+
+namespace {
+cudaError_t launch_k2(const void* images, const ImageSet& set, int K, bool is_float, int nl,
+                      bool sgn, void* partials, void* m2d, cudaStream_t st, const int* gate) {
   K2Params p{};
+  p.gate = gate;
   p.images = images;
   p.set = set;
+  p.nimg = nl * set.P;
   p.K = K;
   p.npairs = num_2d(K);
   p.seg_len = int_seg_len(set);
-  const int64_t nblk = blocks_of(set, is_float, p.blk_base);
+  const int64_t nblk = blocks_of(set, nl, p.blk_base);
   p.partials = partials;
+  const unsigned g = (unsigned)nblk;
   switch (K) {
-#define DPMA_K2_CASE(k)                                                   \
-  case k:                                                                 \
-    if (is_float) k2_f32_seg_kernel<k><<<(unsigned)nblk, kUnitThreads, 0, st>>>(p); \
-    else k2_int_cascade_kernel<k><<<(unsigned)nblk, kUnitThreads, 0, st>>>(p); \
+#define DPMA_K2_CASE(k)                                                              \
+  case k:                                                                            \
+    if (is_float) k2_f32_seg_kernel<k><<<g, kUnitThreads, 0, st>>>(p);               \
+    else if (sgn) k2_int_cascade_kernel<k, true><<<g, kUnitThreads, 0, st>>>(p);     \
+    else k2_int_cascade_kernel<k, false><<<g, kUnitThreads, 0, st>>>(p);             \
     break;
     DPMA_K2_CASE(0) DPMA_K2_CASE(1) DPMA_K2_CASE(2) DPMA_K2_CASE(3) DPMA_K2_CASE(4)
     DPMA_K2_CASE(5) DPMA_K2_CASE(6) DPMA_K2_CASE(7) DPMA_K2_CASE(8)
@@ -373,7 +392,20 @@ cudaError_t launch_image_moments(const void* images, const ImageSet& set, int K,
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_reduce_partials(partials, p.blk_base, set.P, K, is_float, m2d, st);
+  return launch_reduce_partials(partials, p.blk_base, p.nimg, K, is_float, m2d, st, gate);
+}
+}  // namespace
+
+cudaError_t launch_image_moments(const void* images, const ImageSet& set, int K, bool is_float,
+                                 void* partials, void* m2d, cudaStream_t st, const int* gate) {
+  return launch_k2(images, set, K, is_float, 1, false, partials, m2d, st, gate);
+}
+
+cudaError_t launch_image_moments_limbs(const void* images, const ImageSet& set, int64_t limb_stride,
+                                       int K, int nl, void* partials, void* m2d, cudaStream_t st) {
+  ImageSet s2 = set;
+  s2.total_elems = limb_stride;  // the kernel steps from limb to limb by total_elems
+  return launch_k2(images, s2, K, false, nl, true, partials, m2d, st, nullptr);
 }
 
 }  // namespace dpma

@@ -24,9 +24,10 @@ constexpr int kStatusInternal = 7;
 
 struct RedParams {
   const void* partials;
-  int64_t blk_base[kMaxImages + 1];
-  int P, npairs;
+  int64_t blk_base[kMaxLimbImages + 1];
+  int P, npairs;  // P: image rows to reduce
   void* m2d;
+  const int* gate;  // fallback launch: nothing unless (*gate & 3)
 };
 
 // One CTA per (image k, pair t): the threads stride over the image's block
@@ -52,6 +53,7 @@ __global__ void __launch_bounds__(kRedThreads) reduce_int_kernel(RedParams p) {
 }
 
 __global__ void __launch_bounds__(kRedThreads) reduce_f32_kernel(RedParams p) {
+  if (p.gate && (*p.gate & 3) == 0) return;
   const int k = blockIdx.x / p.npairs, t = blockIdx.x % p.npairs;
   const float2* part = static_cast<const float2*>(p.partials);
   float h = 0.f, l = 0.f;
@@ -147,6 +149,7 @@ struct CombParams {
   const void* m2d;
   void* out;
   int* status;
+  const int* gate;  // fallback launch: nothing unless (*gate & 3)
 };
 
 // One warp per moment: the lanes take the terms j = lane, lane + 32, ... of
@@ -190,7 +193,7 @@ __global__ void combine_int_kernel(CombParams p) {
   if (lane != 0) return;
   i128 q = 0;
   if (!div256_exact(acc, D, &q)) {
-    if (p.status) atomicMax(p.status, kStatusInternal);
+    if (p.status) atomicCAS(p.status, 0, kStatusInternal);  // a timeout (5) stays
     q = 0;
   }
   const int mi = n * (n + 1) * (n + 2) / 6 + row;
@@ -198,6 +201,7 @@ __global__ void combine_int_kernel(CombParams p) {
 }
 
 __global__ void combine_f32_kernel(CombParams p) {
+  if (p.gate && (*p.gate & 3) == 0) return;
   int n, row;
   if (!moment_of_warp(p, n, row)) return;
   const int lane = threadIdx.x & 31;
@@ -218,6 +222,119 @@ __global__ void combine_f32_kernel(CombParams p) {
 #pragma unroll
   for (int m = 16; m >= 1; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
   if (lane == 0) static_cast<double*>(p.out)[n * (n + 1) * (n + 2) / 6 + row] = acc / D;
+}
+
+// Float volumes projected on quantisation limbs: the m2d rows hold the exact
+// int128 2-D moments of limb 0 (rows 0..P-1) and limb 1 (rows P..2P-1).
+// One warp per moment combines both limbs exactly, joins them into the
+// moment of the quantised volume, Q = M0 * 2^(B+1) + M1 in units of
+// 2^-(e1+B+1), and converts it to double: the only rounding after the
+// quantisation.  It also bounds the quantisation error of the moment,
+//   |M_pqr(V) - M_pqr(Q)| <= 2^-(e1+B+2) * sum_{x<L} x^p sum_{y<M} y^q sum_{z<N} z^r,
+// each power sum bounded from above in closed form, and raises flag 2 when that bound
+// (plus the final rounding) exceeds `tol` times |M_pqr(Q)| minus the bound,
+// i.e. when the result cannot be guaranteed within tol of the moment of |V|.
+struct FixedParams {
+  const int64_t* plan;
+  int off[kMaxK + 1];
+  int K, npairs, P;
+  const void* m2d;
+  double* out;
+  int* status;
+  int* flags;
+  const int* scale;  // e1, B
+  double L, M, N;
+  double tol;
+};
+
+// Upper bound on sum_{t<n} t^p: n for p = 0, else the last term (n-1)^p plus
+// the integral of t^p over [0, n-1] (t^p increases); zero when n = 1.
+__device__ __forceinline__ double power_sum_bound(double n, int p) {
+  if (p == 0) return n;
+  const double m = n - 1.0;
+  double v = 1.0;
+  for (int i = 0; i < p; ++i) v *= m;
+  return v + v * m / (double)(p + 1);
+}
+
+// double nearest (within a few ulps) to a 256-bit two's complement value
+__device__ __forceinline__ double i256_to_double(I256 a) {
+  const bool neg = (a.w[3] >> 63) != 0;
+  if (neg) neg256(a);
+  double d = (double)a.w[3];
+  d = d * 18446744073709551616.0 + (double)a.w[2];
+  d = d * 18446744073709551616.0 + (double)a.w[1];
+  d = d * 18446744073709551616.0 + (double)a.w[0];
+  return neg ? -d : d;
+}
+
+__global__ void combine_fixed_kernel(FixedParams p) {
+  const int m = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nmom = (p.K + 1) * (p.K + 2) * (p.K + 3) / 6;
+  if (m >= nmom) return;  // uniform across the warp
+  int n = 0;
+  while ((n + 1) * (n + 2) * (n + 3) / 6 <= m) ++n;
+  const int row = m - n * (n + 1) * (n + 2) / 6;
+  const int lane = threadIdx.x & 31;
+  const int64_t* pl = p.plan + p.off[n];
+  const int64_t D = pl[0];
+  const int nm = (int)pl[1];
+  const int64_t* img = pl + 2;
+  const int64_t* aa = img + nm;
+  const int64_t* Cm = aa + nm;
+  const i128* T = static_cast<const i128*>(p.m2d);
+  I256 acc0 = {{0, 0, 0, 0}}, acc1 = {{0, 0, 0, 0}};
+  for (int j = lane; j < nm; j += 32) {
+    const int a = (int)aa[j];
+    const int pair = n * (n + 1) / 2 + (n - a);
+    const int64_t c = Cm[row * nm + j];
+    mac256(acc0, c, T[img[j] * p.npairs + pair]);
+    mac256(acc1, c, T[(p.P + img[j]) * p.npairs + pair]);
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    I256 x, y;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      x.w[w] = __shfl_xor_sync(0xffffffffu, (unsigned long long)acc0.w[w], o);
+      y.w[w] = __shfl_xor_sync(0xffffffffu, (unsigned long long)acc1.w[w], o);
+    }
+    add256(acc0, x);
+    add256(acc1, y);
+  }
+  if (lane != 0) return;
+  i128 q0 = 0, q1 = 0;
+  // a remainder (impossible for images of a volume) also sends the volume
+  // to the fallback, which recomputes it
+  const bool ok = div256_exact(acc0, D, &q0) && div256_exact(acc1, D, &q1);
+  // Q = q0 * 2^(B+1) + q1, exactly, in 256 bits
+  I256 q;
+  {
+    const int sh = p.scale[1] + 1;  // B + 1 <= 22
+    const u128 lo = (u128)q0 << sh;
+    const i128 hi = q0 >> (128 - sh);  // arithmetic: the bits shifted out, sign-extended
+    q.w[0] = (uint64_t)lo;
+    q.w[1] = (uint64_t)(lo >> 64);
+    q.w[2] = (uint64_t)hi;
+    q.w[3] = (uint64_t)(hi >> 64);
+    I256 b;
+    b.w[0] = (uint64_t)(u128)q1;
+    b.w[1] = (uint64_t)((u128)q1 >> 64);
+    b.w[2] = b.w[3] = (q1 < 0) ? ~0ull : 0ull;
+    add256(q, b);
+  }
+  const int e = p.scale[0] + p.scale[1] + 1;  // Q counts units of 2^-e
+  const double val = ldexp(i256_to_double(q), -e);
+  const int mi = n * (n + 1) * (n + 2) / 6 + row;
+  p.out[mi] = val;
+  // (p, q, r) of row `row` of degree n: p descending, then q descending
+  int pp = n, rr = row;
+  while (rr > n - pp) { rr -= n - pp + 1; --pp; }
+  const int qq = n - pp - rr, rz = rr;
+  const double bound = ldexp(power_sum_bound(p.L, pp) * power_sum_bound(p.M, qq) *
+                                 power_sum_bound(p.N, rz), -e - 1) +
+                       fabs(val) * 0x1p-50;
+  if (!ok || !(bound <= p.tol * (fabs(val) - bound))) atomicOr(p.flags, 2);
 }
 
 struct DevPlan {
@@ -261,7 +378,8 @@ cudaError_t device_plan(int K, DevPlan* out) {
 }  // namespace
 
 namespace {
-__global__ void clear_kernel(uint32_t* p, int64_t n32, int* status) {
+__global__ void clear_kernel(uint32_t* p, int64_t n32, int* status, const int* gate) {
+  if (gate && (*gate & 3) == 0) return;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if (status && gid == 0) *status = 0;
@@ -272,8 +390,9 @@ __global__ void clear_kernel(uint32_t* p, int64_t n32, int* status) {
 }
 }  // namespace
 
-cudaError_t launch_clear(void* p, size_t bytes, int* status, cudaStream_t st) {
+cudaError_t launch_clear(void* p, size_t bytes, int* status, cudaStream_t st, const int* gate) {
   if ((reinterpret_cast<uintptr_t>(p) & 15) != 0 || (bytes & 3) != 0) {
+    if (gate) return cudaErrorInvalidValue;  // gated clears need the kernel
     cudaError_t e = cudaMemsetAsync(p, 0, bytes, st);
     if (e == cudaSuccess && status) e = cudaMemsetAsync(status, 0, sizeof(int), st);
     return e;
@@ -286,13 +405,14 @@ cudaError_t launch_clear(void* p, size_t bytes, int* status, cudaStream_t st) {
   const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * 8;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  clear_kernel<<<(unsigned)blocks, 256, 0, st>>>(static_cast<uint32_t*>(p), n32, status);
+  clear_kernel<<<(unsigned)blocks, 256, 0, st>>>(static_cast<uint32_t*>(p), n32, status, gate);
   return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_partials(const void* partials, const int64_t* blk_base, int P, int K,
-                                   bool is_float, void* m2d, cudaStream_t st) {
+                                   bool is_float, void* m2d, cudaStream_t st, const int* gate) {
   RedParams p{};
+  p.gate = gate;
   p.partials = partials;
   p.m2d = m2d;
   for (int k = 0; k <= P; ++k) p.blk_base[k] = blk_base[k];
@@ -311,11 +431,12 @@ cudaError_t prepare_combine(int K) {
 }
 
 cudaError_t launch_combine(const void* m2d, int K, bool is_float, void* out, int* status,
-                           cudaStream_t st) {
+                           cudaStream_t st, const int* gate) {
   DevPlan dp{};
   cudaError_t e = device_plan(K, &dp);
   if (e != cudaSuccess) return e;
   CombParams p{};
+  p.gate = gate;
   p.plan = dp.words;
   for (int n = 0; n <= kMaxK; ++n) p.off[n] = dp.off[n];
   p.K = K;
@@ -328,6 +449,32 @@ cudaError_t launch_combine(const void* m2d, int K, bool is_float, void* out, int
   const int blocks = (nmom * 32 + threads - 1) / threads;
   if (is_float) combine_f32_kernel<<<blocks, threads, 0, st>>>(p);
   else combine_int_kernel<<<blocks, threads, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine_fixed(const void* m2d, int K, int P, double* out, int* status,
+                                 int* flags, const int* scale, int64_t L, int64_t M, int64_t N,
+                                 double tol, cudaStream_t st) {
+  DevPlan dp{};
+  cudaError_t e = device_plan(K, &dp);
+  if (e != cudaSuccess) return e;
+  FixedParams p{};
+  p.plan = dp.words;
+  for (int n = 0; n <= kMaxK; ++n) p.off[n] = dp.off[n];
+  p.K = K;
+  p.npairs = num_2d(K);
+  p.P = P;
+  p.m2d = m2d;
+  p.out = out;
+  p.status = status;
+  p.flags = flags;
+  p.scale = scale;
+  p.L = (double)L; p.M = (double)M; p.N = (double)N;
+  p.tol = tol;
+  const int nmom = num_moments(K);
+  const int threads = 128;
+  const int blocks = (nmom * 32 + threads - 1) / threads;
+  combine_fixed_kernel<<<blocks, threads, 0, st>>>(p);
   return cudaGetLastError();
 }
 

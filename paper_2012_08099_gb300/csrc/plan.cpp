@@ -293,4 +293,19 @@ double log2_bound_3d(int64_t L, int64_t M, int64_t N, double vmax, int K) {
   return worst;
 }
 
+int float_limb_bits(int64_t L, int64_t M, int64_t N, int K) {
+  // every line holds at most max(L, M, N) voxels: line sums of limbs up to
+  // 2^B stay below 2^30
+  const int64_t nmax = std::max<int64_t>(L, std::max<int64_t>(M, N));
+  int lg = 0;
+  while (((int64_t)1 << lg) < nmax) ++lg;
+  int B = 30 - lg;
+  if (B > 22) B = 22;  // the rounding by 1.5 * 2^23 needs |x| <= 2^22
+  // limb moments (2-D and 3-D) of a volume of values up to 2^B within int128
+  const double unit = std::max(log2_bound_2d(L, M, N, 1.0, K), log2_bound_3d(L, M, N, 1.0, K));
+  const int cap = (int)std::floor(124.0 - unit);
+  if (B > cap) B = cap;
+  return B;
+}
+
 }  // namespace dpma

@@ -740,6 +740,8 @@ dpma_status dpma_server_submit(dpma_server* s, const dpma_volume_desc* desc, uin
 
 dpma_status dpma_server_submit_keyed(dpma_server* s, const dpma_volume_desc* desc, uint64_t key,
                                      uint64_t* ticket) {
+  // latency runs from entry to this call (before the pinned copy) to completion
+  const double t_entry = now_ms();
   if (!s || !desc || !ticket) return sfail(DPMA_ERR_INVALID_ARG, "null argument");
   dpma_volume_desc d = *desc;
   d.out_offset = 0;
@@ -782,7 +784,7 @@ dpma_status dpma_server_submit_keyed(dpma_server* s, const dpma_volume_desc* des
   r->d.volume = r->h_in;
   std::lock_guard<std::mutex> lk(s->mu);
   r->id = s->next_id++;
-  r->t_submit = now_ms();
+  r->t_submit = t_entry;
   if (s->t_first_submit < 0) s->t_first_submit = r->t_submit;
   s->n_submitted++;
   s->reqs[r->id] = r;

@@ -1,0 +1,186 @@
+"""GPU parity of the integer-lane projection (volumes with 16-byte aligned rows).
+
+Integer volumes: images and moments bit for bit against the oracle.  Float32
+volumes are quantised onto two int32 limbs and projected exactly; their
+moments must satisfy |M_gpu - M_oracle| <= 1e-6 * M_pqr(|V|), and for these
+volumes the quantised pipeline itself must have produced them (no fallback).
+Volumes with a dynamic range beyond the quantisation grid must take the
+compensated fallback and still meet the tolerance.  A bounded device wait
+that is made to run out must come back as DPMA_ERR_TIMEOUT.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2012_08099_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def dpma():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2012_08099_gb300 as d
+    d.lib()
+    return d
+
+
+def dev(vol):
+    import paper_2012_08099_gb300 as d
+    if vol.dtype == np.uint16:
+        return torch.from_numpy(vol.view(np.int16)).cuda(), d.U16
+    if vol.dtype == np.uint8:
+        return torch.from_numpy(vol).cuda(), d.U8
+    return torch.from_numpy(vol).cuda(), d.F32
+
+
+# (N, M, L) with L a multiple of 16: rows are 16-byte aligned for every
+# element type.  They span several 64-column tiles and 48/64-row bands,
+# ragged in x, y and z, odd and even N (z-pairs), and single slices.
+SHAPES = [
+    (1, 1, 16), (2, 5, 16), (1, 9, 32), (3, 1, 48), (9, 70, 80), (17, 97, 208),
+    (33, 130, 192), (64, 64, 64), (65, 50, 144), (4, 200, 272),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_lane_images_bit_exact(dpma, shape, dtype):
+    vol = synth.uniform_volume(shape, dtype, seed=sum(shape) + 17)
+    t, dt = dev(vol)
+    for K in (2, 3, 4, 5, 6):
+        got = dpma.project(t, K, dt)
+        want = oracle.project(vol, oracle.num_images(K))
+        for k, (g, w) in enumerate(zip(got, want)):
+            np.testing.assert_array_equal(g, w, err_msg=f"image {k} K={K} {shape}")
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_lane_moments_bit_exact(dpma, shape, dtype):
+    vol = synth.uniform_volume(shape, dtype, seed=3 * sum(shape) + 1)
+    t, dt = dev(vol)
+    for K in range(9):
+        assert dpma.moments_values(t, K, dt) == oracle.moments(vol, K), f"K={K} {shape}"
+
+
+def test_lane_u16_phantom_k6(dpma):
+    vol = synth.ct_phantom_u16(96, 80, 50, seed=2, axis_scale=0.4)
+    t, dt = dev(vol)
+    assert dpma.moments_values(t, 6, dt) == oracle.moments(vol, 6)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("kind", ["uniform", "signed", "mri"])
+def test_lane_float_moments(dpma, shape, kind):
+    N, M, L = shape
+    if kind == "mri":
+        vol = synth.mri_like_f32(L, M, N, seed=sum(shape), n_blobs=6)
+    elif kind == "signed":
+        vol = synth.uniform_volume(shape, np.float32, sum(shape), low=-1.0, high=1.0)
+    else:
+        vol = synth.uniform_volume(shape, np.float32, sum(shape))
+    t, dt = dev(vol)
+    for K in (0, 1, 3, 4, 6):
+        got = dpma.moments_values(t, K, dt)
+        assert dpma.last_float_path() == 0, f"K={K} {shape} took the fallback"
+        want = oracle.moments(vol, K)
+        mag = oracle.moments(vol, K, absolute=True)
+        err = np.abs(got - want)
+        assert np.all(err <= TOL * mag), (K, shape, float(np.max(err / np.maximum(mag, 1e-300))))
+
+
+def test_lane_float_full_range_goes_to_fallback(dpma):
+    """One voxel 2^40 times the rest: the quantisation grid that holds it
+    cannot resolve the others within the tolerance, so the compensated
+    pipeline recomputes the volume."""
+    vol = synth.uniform_volume((20, 40, 64), np.float32, 5, low=0.5, high=1.0)
+    vol[7, 11, 13] = 2.0 ** 40
+    t, dt = dev(vol)
+    got = dpma.moments_values(t, 4, dt)
+    assert dpma.last_float_path() != 0
+    want = oracle.moments(vol, 4)
+    mag = oracle.moments(vol, 4, absolute=True)
+    assert np.all(np.abs(got - want) <= TOL * mag)
+
+
+def test_lane_float_voxel_beyond_sampled_grid(dpma):
+    """A hot voxel in a row the magnitude sample skips leaves the grid: the
+    range flag sends the volume to the fallback."""
+    N, M, L = 64, 128, 64          # 8192 rows: every other row is sampled
+    vol = synth.uniform_volume((N, M, L), np.float32, 9, low=0.5, high=1.0)
+    rows = M * N
+    nsr = 4096
+    step = rows // nsr
+    sampled = {j * rows // nsr + ((j * 7919) % step if step > 1 else 0) for j in range(nsr)}
+    row = next(r for r in range(rows // 2, rows) if r not in sampled)
+    vol[row // M, row % M, 5] = 1.0e6
+    t, dt = dev(vol)
+    got = dpma.moments_values(t, 3, dt)
+    assert dpma.last_float_path() & 1
+    want = oracle.moments(vol, 3)
+    mag = oracle.moments(vol, 3, absolute=True)
+    assert np.all(np.abs(got - want) <= TOL * mag)
+
+
+@pytest.mark.parametrize("dtype", [np.uint16, np.float32])
+def test_lane_host_path_in_chunks(dpma, dtype):
+    """dpma_moments_host copies the volume in even z-chunks and projects each
+    as it lands (the float grid comes from the first chunk)."""
+    shape = (301, 40, 48)
+    if dtype == np.float32:
+        vol = synth.mri_like_f32(48, 40, 301, seed=4, n_blobs=5)
+    else:
+        vol = synth.uniform_volume(shape, dtype, seed=4)
+    got = dpma.moments_host(vol, 6)
+    if dtype == np.float32:
+        assert dpma.last_float_path() == 0
+        want = oracle.moments(vol, 6)
+        mag = oracle.moments(vol, 6, absolute=True)
+        assert np.all(np.abs(np.asarray(got) - want) <= TOL * mag)
+    else:
+        assert dpma.int128_to_ints(got) == oracle.moments(vol, 6)
+
+
+def test_lane_async_fallback_gate(dpma):
+    """dpma_moments_async on a float volume that needs the fallback: the
+    gated compensated kernels on the same stream give the right result."""
+    vol = synth.uniform_volume((12, 30, 32), np.float32, 21, low=0.5, high=1.0)
+    vol[3, 4, 5] = 2.0 ** 40
+    t, dt = dev(vol)
+    nm = dpma.num_moments(4)
+    out = torch.empty(nm, dtype=torch.float64, device="cuda")
+    dpma.moments_async(t, 4, out, dt)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    want = oracle.moments(vol, 4)
+    mag = oracle.moments(vol, 4, absolute=True)
+    assert np.all(np.abs(got - want) <= TOL * mag)
+
+
+@pytest.mark.parametrize("dtype", [np.uint16, np.float32])
+def test_bounded_wait_runs_out(dpma, dtype):
+    """With a one-cycle wait budget the first pending copy of every CTA is not
+    waited for: the kernel lets its copies land, leaves, and the call returns
+    DPMA_ERR_TIMEOUT; the default budget then gives exact results again."""
+    vol = synth.uniform_volume((40, 96, 128), dtype, seed=6)
+    t, dt = dev(vol)
+    dpma.set_wait_budget(1)
+    try:
+        with pytest.raises(dpma.DpmaError) as e:
+            dpma.moments(t, 4, dt)
+        assert e.value.status == 5
+    finally:
+        dpma.set_wait_budget(0)
+    got = dpma.moments_values(t, 4, dt)
+    want = oracle.moments(vol, 4)
+    if dtype == np.float32:
+        mag = oracle.moments(vol, 4, absolute=True)
+        assert np.all(np.abs(got - want) <= TOL * mag)
+    else:
+        assert got == want
