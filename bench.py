@@ -35,8 +35,10 @@ L = M = N = 512
 K = 6
 SEED = 3
 WORKLOAD = "mri_like_f32_512x512x512_K6"
-KERNEL_SRC = os.path.join(ROOT, "paper_2012_08099_gb300", "csrc", "k1_project.cuh")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k1_project_mri512_f32_k6_traffic.json")
+CASE = "f32"  # volume recipe: f32 MRI-like, u16 CT-like phantom, u8 uniform
+KERNEL_SRC = os.path.join(ROOT, "paper_2012_08099_gb300", "csrc", "k1_int.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k1_int_mri512_f32_k6_traffic.json")
+K1_NAME = "k1_int_kernel (fused projection; float32 as two quantised int32 limbs)"
 
 
 def parse():
@@ -49,16 +51,34 @@ def parse():
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-single-rows", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=400)
     ap.add_argument("--shape", default=None,
                     help="L,M,N of a smaller volume of the same recipe (profiling runs)")
+    ap.add_argument("--case", default=None,
+                    help="dtype:K of a profiling run (u16 = CT-like phantom, u8 = uniform "
+                         "0-255, f32 = MRI-like); the headline line is f32:6")
     args = ap.parse_args()
+    global L, M, N, WORKLOAD, CASE, K
     if args.shape:
-        global L, M, N, WORKLOAD
         L, M, N = (int(v) for v in args.shape.split(","))
-        WORKLOAD = f"mri_like_f32_{L}x{M}x{N}_K{K}"
+    if args.case:
+        CASE, k = args.case.split(":")
+        K = int(k)
+    if args.shape or args.case:
+        recipe = {"f32": "mri_like_f32", "u16": "ct_phantom_u16", "u8": "uniform_u8"}[CASE]
+        WORKLOAD = f"{recipe}_{L}x{M}x{N}_K{K}"
     return args
+
+
+def make_volume(seed):
+    from paper_2012_08099_gb300 import synth
+    if CASE == "u16":
+        return synth.ct_phantom_u16(L, M, N, seed=seed)
+    if CASE == "u8":
+        return synth.uniform_volume((N, M, L), np.uint8, seed=seed)
+    return synth.mri_like_f32(L, M, N, seed=seed)
 
 
 def dist_info():
@@ -161,17 +181,37 @@ def cpu_baseline(vol: np.ndarray, budget_s: float):
                       f"{vox} voxels in {dt:.2f} s"}
 
 
+def cpu_dpma_baseline(vol: np.ndarray, reps: int = 5):
+    """The multithreaded CPU DPMA (projections, 1-D integrals, exact
+    combine) on the whole volume, all host cores; median of `reps` runs."""
+    import cpu_dpma
+    cpu_dpma.moments(vol, K)  # plan and page-in
+    ts = []
+    used = 0
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        _, used = cpu_dpma.moments(vol, K, return_threads=True)
+        ts.append(time.perf_counter() - t0)
+    dt = statistics.median(ts)
+    return {"value": vol.size / dt, "unit": UNIT, "cores": used, "kind": "cpu_dpma",
+            "sample": f"the whole {WORKLOAD} volume ({vol.size} voxels), median of {reps} runs "
+                      f"of {dt:.3f} s"}
+
+
 # ------------------------------------------------------------------- ours
 
 
-def traffic_if_current():
+def counters_if_current():
+    """ncu counters of the projection kernel for this workload, per launch
+    (dram bytes, warp instructions), if they were taken on the kernel source
+    as it stands; else None."""
     try:
         with open(TRAFFIC_FILE) as f:
             rec = json.load(f)
         with open(KERNEL_SRC, "rb") as f:
             h = hashlib.sha256(f.read()).hexdigest()
-        if rec.get("k1_project_sha256") == h:
-            return float(rec["dram_bytes_per_launch"])
+        if rec.get("k1_int_sha256") == h:
+            return rec
     except Exception:
         pass
     return None
@@ -196,18 +236,19 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     lib = dpma.lib()
-    vol = synth.mri_like_f32(L, M, N, seed=SEED + rank)
-    t = torch.from_numpy(vol).cuda()
+    vol = make_volume(SEED + rank)
+    DT = {"f32": dpma.F32, "u16": dpma.U16, "u8": dpma.U8}[CASE]
+    t = torch.from_numpy(vol.view(np.int16) if vol.dtype == np.uint16 else vol).cuda()
     nm = dpma.num_moments(K)
-    ws = torch.empty(dpma.workspace_size(L, M, N, dpma.F32, K), dtype=torch.uint8, device="cuda")
-    out = torch.empty(nm, dtype=torch.float64, device="cuda")
+    ws = torch.empty(dpma.workspace_size(L, M, N, DT, K), dtype=torch.uint8, device="cuda")
+    out = torch.empty(nm * 2, dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
     sp = ctypes.c_void_p(stream.cuda_stream)
     vp, op, wp = (ctypes.c_void_p(x.data_ptr()) for x in (t, out, ws))
     wbytes = ws.numel()
 
     def step():
-        rc = lib.dpma_moments_async(vp, L, M, N, dpma.F32, K, op, sp, wp, wbytes)
+        rc = lib.dpma_moments_async(vp, L, M, N, DT, K, op, sp, wp, wbytes)
         if rc:
             raise dpma.DpmaError(rc, lib.dpma_last_error().decode())
 
@@ -245,42 +286,45 @@ def run_ours(args):
     # roofline of the dominant kernel (fused projection): algorithmic bytes =
     # every voxel read once
     k1_ms = stage_ms[1] / args.steps
-    algo_bytes = voxels * 4
+    algo_bytes = float(vol.nbytes)
     peak, peak_kind = measured_hbm_peak()
     achieved = algo_bytes / (k1_ms * 1e-3) / 1e9
+    ctr = counters_if_current() if (L, M, N) == (512, 512, 512) else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic_if_current() if (L, M, N) == (512, 512, 512) else None,
+                "frac": round(achieved / peak, 4),
+                "traffic": float(ctr["dram_bytes_per_launch"]) if ctr else None,
                 "peak_source": f"{peak_kind} hbm_gbs",
-                "kernel": "k1_project (fused projection)", "kernel_ms": round(k1_ms, 5),
+                "kernel": K1_NAME, "kernel_ms": round(k1_ms, 5),
                 "pipeline_frac": round(algo_bytes / (ms_step * 1e-3) / 1e9 / peak, 4),
-                "stage_ms_per_step": [round(s / args.steps, 5) for s in stage_ms]}
+                "stage_ms_per_step": [round(s / args.steps, 5) for s in stage_ms],
+                "stage_launches_per_step": [round(n / args.steps, 3) for n in stage_launches]}
     gpu_launches = int(sum(stage_launches))
-    # The float projection is bound by its compensated additions, not by HBM:
-    # each voxel enters P images, each through an error-free TwoSum plus the
-    # compensation add (7 FP32 additions).  Peak: FP32 add lanes (128 per SM)
-    # x SMs x the SM clock sampled during the timed region.
+    # The integer-lane projection does its exact sums on the integer/ALU
+    # pipes; what bounds it is instruction issue: 4 schedulers per SM, one
+    # warp instruction each per clock.  Instructions per launch come from the
+    # ncu capture of the same kernel source (scaled to 512 slices).
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    alu_roofline = None
-    if clk and clk.get("sm_mhz"):
-        flops = voxels * 7 * dpma.num_images(K)
-        alu_peak = sms * 128 * clk["sm_mhz"] * 1e6 / 1e12
-        alu_ach = flops / (k1_ms * 1e-3) / 1e12
-        alu_roofline = {"bound": "alu", "achieved": round(alu_ach, 2), "peak": round(alu_peak, 2),
-                        "unit": "TFLOP/s", "frac": round(alu_ach / alu_peak, 4),
-                        "kernel": "k1_project (fused projection)",
-                        "flops_per_voxel": 7 * dpma.num_images(K),
-                        "peak_source": f"{sms} SMs x 128 FP32 lanes x median SM clock"}
+    issue_roofline = None
+    if clk and clk.get("sm_mhz") and ctr and ctr.get("warp_inst_per_launch"):
+        inst = float(ctr["warp_inst_per_launch"])
+        ipk = sms * 4 * clk["sm_mhz"] * 1e6 / 1e12
+        ach = inst / (k1_ms * 1e-3) / 1e12
+        issue_roofline = {"bound": "issue", "achieved": round(ach, 4), "peak": round(ipk, 4),
+                          "unit": "Twarp-inst/s", "frac": round(ach / ipk, 4), "kernel": K1_NAME,
+                          "thread_inst_per_voxel": round(inst * 32 / voxels, 2),
+                          "peak_source": f"{sms} SMs x 4 schedulers x median SM clock"}
 
     # end to end through the C ABI from pinned host memory
-    hv = torch.from_numpy(vol).pin_memory()
-    ho = torch.empty(nm, dtype=torch.float64).pin_memory()
+    hv = torch.from_numpy(vol.view(np.int16) if vol.dtype == np.uint16 else vol).pin_memory()
+    out_bytes = nm * (8 if CASE == "f32" else 16)
+    ho = torch.empty(nm * 2, dtype=torch.float64).pin_memory()
     hvp, hop = ctypes.c_void_p(hv.data_ptr()), ctypes.c_void_p(ho.data_ptr())
     for _ in range(3):
-        lib.dpma_moments_host(hvp, L, M, N, dpma.F32, K, hop)
+        lib.dpma_moments_host(hvp, L, M, N, DT, K, hop)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        rc = lib.dpma_moments_host(hvp, L, M, N, dpma.F32, K, hop)
+        rc = lib.dpma_moments_host(hvp, L, M, N, DT, K, hop)
         if rc:
             raise dpma.DpmaError(rc, lib.dpma_last_error().decode())
     barrier()
@@ -290,10 +334,12 @@ def run_ours(args):
         dist.all_reduce(x, op=dist.ReduceOp.MAX)
         e2e_s = float(x.item())
     e2e = {"value": world * voxels / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(vol.nbytes), "d2h_bytes_per_step": int(nm * 8 + 4),
+           "h2d_bytes_per_step": int(vol.nbytes), "d2h_bytes_per_step": int(out_bytes + 8),
            "ms_per_step": round(e2e_s * 1e3, 4)}
 
-    batched = serving = None
+    batched = serving = singles = None
+    if rank == 0 and not args.no_single_rows:
+        singles = run_single_rows(dpma, torch, peak)
     if rank == 0 and not args.no_batched:
         batched = run_batched(dpma, torch)
     if rank == 0 and not args.no_serving:
@@ -302,25 +348,138 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(vol, args.cpu_budget_s)
+        cpu["cpu_dpma"] = cpu_dpma_baseline(vol)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
+            "dtype": {"f32": "f32", "u16": "u16", "u8": "u8"}[CASE], "data": "synthetic",
             "config": {"workload": WORKLOAD, "L": L, "M": M, "N": N, "K": K,
                        "moments": nm, "images": dpma.num_images(K),
                        "volume_bytes": int(vol.nbytes), "parallelism": f"replicas{world}",
                        "l2": f"input {vol.nbytes / 1e6:.0f} MB vs 129 MB L2"
                              + (" (larger: no flush needed)" if vol.nbytes > 129e6 else "")},
-            "roofline": roofline, "alu_roofline": alu_roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "issue_roofline": issue_roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": gpu_launches, "clocks": clk,
-            "batched": batched, "serving": serving,
+            "single_volume_rows": singles, "batched": batched, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------ single-volume rows
+
+
+def run_single_rows(dpma, torch, peak):
+    """The two smaller single-volume workloads: 64^3 u8 (uniform 0-255) at
+    K = 3, and the 256^3 u16 CT-like phantom at K = 6.  Both fit in the
+    129 MB L2, so every timed call of the phantom follows a 256 MB write
+    that flushes it; the 64^3 volume (256 KB) is timed as a call rate
+    (back-to-back asynchronous calls) and as the latency of the synchronous
+    call, each with the projection kernel's own event time."""
+    from paper_2012_08099_gb300 import synth
+    lib = dpma.lib()
+    rows = []
+    s = torch.cuda.Stream()
+    sp = ctypes.c_void_p(s.cuda_stream)
+
+    def setup(vol, dt, K):
+        t = torch.from_numpy(vol.view(np.int16) if vol.dtype == np.uint16 else vol).cuda()
+        L_, M_, N_ = vol.shape[2], vol.shape[1], vol.shape[0]
+        ws = torch.empty(dpma.workspace_size(L_, M_, N_, dt, K), dtype=torch.uint8, device="cuda")
+        out = torch.empty(dpma.num_moments(K) * 2, dtype=torch.int64, device="cuda")
+        args = (ctypes.c_void_p(t.data_ptr()), L_, M_, N_, dt, K, ctypes.c_void_p(out.data_ptr()),
+                sp, ctypes.c_void_p(ws.data_ptr()), ws.numel())
+
+        def call():
+            rc = lib.dpma_moments_async(*args)
+            if rc:
+                raise dpma.DpmaError(rc, lib.dpma_last_error().decode())
+        return t, out, call
+
+    def k1_stage(call, reps, between=None):
+        dpma.stage_timing(True)
+        dpma.stage_times(reset=True)
+        with torch.cuda.stream(s):
+            for _ in range(reps):
+                if between:
+                    between()
+                call()
+        s.synchronize()
+        ms, n = dpma.stage_times(reset=True)
+        dpma.stage_timing(False)
+        return [m / reps for m in ms], [x / reps for x in n]
+
+    # 64^3 u8, K = 3
+    vol = synth.uniform_volume((64, 64, 64), np.uint8, seed=1)
+    t, out, call = setup(vol, dpma.U8, 3)
+    with torch.cuda.stream(s):
+        for _ in range(20):
+            call()
+    s.synchronize()
+    reps = 2000
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s):
+        e0.record(s)
+        for _ in range(reps):
+            call()
+        e1.record(s)
+    e1.synchronize()
+    us_async = e0.elapsed_time(e1) * 1e3 / reps
+    lat = []
+    for _ in range(300):
+        t0 = time.perf_counter()
+        dpma.moments(t, 3, dpma.U8, out=out.view(-1, 2))
+        lat.append((time.perf_counter() - t0) * 1e6)
+    st_ms, st_n = k1_stage(call, 500)
+    k1_us = st_ms[1] * 1e3
+    rows.append({"workload": "uniform_u8_64x64x64_K3", "metric": "us per call",
+                 "us_per_call_async": round(us_async, 3),
+                 "us_per_call_sync_p50": round(statistics.median(lat), 2),
+                 "k1_us": round(k1_us, 3),
+                 "stage_us": [round(m * 1e3, 3) for m in st_ms],
+                 "roofline": {"bound": "hbm", "achieved": round(vol.nbytes / (k1_us * 1e-6) / 1e9, 1),
+                              "peak": peak, "unit": "GB/s",
+                              "frac": round(vol.nbytes / (k1_us * 1e-6) / 1e9 / peak, 4),
+                              "note": "256 KB volume, L2-resident between calls"},
+                 "gpu_launches_per_call": sum(st_n)})
+
+    # 256^3 u16 CT-like phantom, K = 6, L2 flushed before every call
+    vol = synth.ct_phantom_u16(256, 256, 256, seed=2)
+    t, out, call = setup(vol, dpma.U16, 6)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def do_flush():
+        flush.fill_(1)
+    with torch.cuda.stream(s):
+        for _ in range(5):
+            call()
+    s.synchronize()
+    reps = 200
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(reps)]
+    with torch.cuda.stream(s):
+        for a, b in evs:
+            do_flush()
+            a.record(s)
+            call()
+            b.record(s)
+    s.synchronize()
+    us_call = statistics.median(a.elapsed_time(b) for a, b in evs) * 1e3
+    st_ms, st_n = k1_stage(call, 100, do_flush)
+    k1_us = st_ms[1] * 1e3
+    ach = vol.nbytes / (k1_us * 1e-6) / 1e9
+    rows.append({"workload": "ct_phantom_u16_256x256x256_K6", "metric": "voxel/s",
+                 "value": vol.size / (us_call * 1e-6), "us_per_call_p50": round(us_call, 2),
+                 "k1_us": round(k1_us, 3), "stage_us": [round(m * 1e3, 3) for m in st_ms],
+                 "l2": "256 MB buffer written before every timed call (L2 flush)",
+                 "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak,
+                              "unit": "GB/s", "frac": round(ach / peak, 4)},
+                 "gpu_launches_per_call": sum(st_n)})
+    return rows
 
 
 # ------------------------------------------------ batched and serving rows
@@ -465,7 +624,7 @@ def run_reference(args):
     import oracle
 
     oracle.build()
-    vol = synth.mri_like_f32(L, M, N, seed=SEED)
+    vol = make_volume(SEED)
     threads = os.cpu_count() or 1
     per_slice = oracle_rate(np.ascontiguousarray(vol[:2]), threads) / 2.0
     budget = 150.0 / max(1, args.steps + args.warmup)

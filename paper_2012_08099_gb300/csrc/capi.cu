@@ -163,6 +163,7 @@ cudaError_t ensure_buffer(void** p, size_t* have, size_t need) {
 // Optional per-stage event timing (profiling aid, off by default).
 struct StageEvent {
   int stage;
+  int kernels;  // kernel launches the stage made
   cudaEvent_t a, b;
 };
 std::mutex g_timing_mu;
@@ -171,9 +172,6 @@ std::vector<StageEvent> g_pending;
 std::vector<cudaEvent_t> g_free_events;
 double g_stage_ms[4] = {0, 0, 0, 0};
 int64_t g_stage_launches[4] = {0, 0, 0, 0};
-// kernel launches each stage makes: clear, projection, image moments +
-// partial reduction, combine
-constexpr int kStageKernels[4] = {1, 1, 2, 1};
 
 cudaEvent_t take_event() {
   if (!g_free_events.empty()) {
@@ -195,12 +193,12 @@ struct StageRecorder {
     on = g_timing;
     if (on) { last = take_event(); cudaEventRecord(last, st); }
   }
-  void mark(int stage) {
+  void mark(int stage, int kernels) {
     if (!on) return;
     std::lock_guard<std::mutex> lk(g_timing_mu);
     cudaEvent_t e = take_event();
     cudaEventRecord(e, st);
-    g_pending.push_back({stage, last, e});
+    g_pending.push_back({stage, kernels, last, e});
     last = take_event();
     cudaEventRecord(last, st);
   }
@@ -279,6 +277,7 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
   const bool lanes = project_int_supported(volume, L, (int)dtype, w.set.P) &&
                      (!fl || B >= kMinLimbBits);
   int ia_nsample = 0;
+  int k1_launches = 0;
   if (!lanes) {
     e = launch_clear(images, w.img_bytes, status, st);
   } else {
@@ -290,7 +289,7 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
                             0, N, fl && !host_src ? sample : nullptr, &ia_nsample, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "clear images");
-  rec.mark(0);
+  rec.mark(0, 1);
   ProjectArgs a{};
   a.vol = volume;
   a.L = L; a.M = M; a.N = N;
@@ -328,12 +327,14 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
       if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
       if (e != cudaSuccess) return cuda_fail(e, "copy volume chunk to device");
       if (lanes && fl && z0 == 0) {
-        // the quantisation grid from the first chunk (8x headroom; a later
+        // the quantisation grid from the first chunk (2x headroom; a later
         // voxel beyond it raises the fallback)
         e = launch_clear_sample(images, 0, nullptr, nullptr, static_cast<const float*>(volume),
                                 L, M, 0, nz, sample, &ia.nsample, st);
         if (e != cudaSuccess) return cuda_fail(e, "magnitude sample");
+        ++k1_launches;
       }
+      ++k1_launches;
       if (lanes) {
         ia.z0 = z0;
         ia.nz = nz;
@@ -353,25 +354,29 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
       e = launch_project(a, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "projection kernel");
+    k1_launches = 1;
   }
-  rec.mark(1);
+  rec.mark(1, k1_launches);
   if (lanes && fl) {
     e = launch_image_moments_limbs(images, w.set, w.set.total_elems, K, 2, ws + w.off_part,
                                    ws + w.off_m2d, st);
     if (e != cudaSuccess) return cuda_fail(e, "image moment kernel");
-    rec.mark(2);
+    rec.mark(2, 2);
     e = launch_combine_fixed(ws + w.off_m2d, K, w.set.P, static_cast<double*>(out), status, flags,
                              scale, L, M, N, kFloatTolerance, st);
     if (e != cudaSuccess) return cuda_fail(e, "combine kernel");
-    rec.mark(3);
-    return enqueue_float_fallback(volume, L, M, N, K, out, st, ws, w);
+    // the combine and the five gated fallback launches (clear, projection,
+    // image moments + reduction, combine) count as the last stage
+    const dpma_status fs = enqueue_float_fallback(volume, L, M, N, K, out, st, ws, w);
+    rec.mark(3, 6);
+    return fs;
   }
   e = launch_image_moments(images, w.set, K, fl, ws + w.off_part, ws + w.off_m2d, st);
   if (e != cudaSuccess) return cuda_fail(e, "image moment kernel");
-  rec.mark(2);
+  rec.mark(2, 2);
   e = launch_combine(ws + w.off_m2d, K, fl, out, status, st);
   if (e != cudaSuccess) return cuda_fail(e, "combine kernel");
-  rec.mark(3);
+  rec.mark(3, 1);
   return DPMA_OK;
 }
 
@@ -679,7 +684,7 @@ dpma_status dpma_stage_times(double* ms, int64_t* launches, int reset) {
       return cuda_fail(e, "stage timing events");
     }
     g_stage_ms[se.stage] += t;
-    g_stage_launches[se.stage] += kStageKernels[se.stage];
+    g_stage_launches[se.stage] += se.kernels;
     g_free_events.push_back(se.a);
     g_free_events.push_back(se.b);
   }

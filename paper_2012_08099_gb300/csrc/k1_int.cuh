@@ -37,13 +37,14 @@
 //     lanes along y, lane gl owning RYB = 8 consecutive rows of BB columns;
 //     images 0 (x, y), 2 (sum along y) and 5/6 (y+-z, x).
 // Images whose lines leave the slice accumulate in registers across z in
-// windows of 9 pixels per owned row (3/4) or column (5/6): the two slices of
-// a step land on neighbouring pixels, so a pixel takes both voxels in one
-// 3-input add; after the step the two pixels that leave a lane's window go
-// to its neighbour lane.  At the tile edge they are complete for this tile:
-// images 3/4 stage them into runs of 16 consecutive pixels, merged by one
-// coalesced reduction every 8 steps; images 5/6 stage the edge rows for one
-// warp to merge after the next barrier.  Images whose lines lie in the slice
+// windows of RA pixels per owned row (3/4) or RYB pixels per owned column
+// (5/6): the two slices of a step land on neighbouring pixels, so a pixel
+// takes both voxels in one 3-input add; after the step the two pixels that
+// leave a lane's window go to its neighbour lane.  At the tile edge they are
+// complete for this tile: images 3/4 stage them into runs of 16 consecutive
+// pixels, merged by one coalesced reduction every 8 steps; images 5/6 stage
+// the edge rows, which all warps of group B merge together after the next
+// barrier.  Images whose lines lie in the slice
 // (1 and 2) are reduced per step across the lane group.  Partial pixels go to
 // the images in L2 with red.global.add.u32 (wrapping 32-bit adds are exact
 // because every complete pixel fits in int32).
@@ -218,12 +219,18 @@ template <int W> __device__ __forceinline__ void load_row(const uint8_t* p, uint
 }
 
 // Sum over a group of G aligned lanes (G a power of two, the group given by
-// `gl` = lane % G) of NV values per lane.  The values are scattered while they
-// are reduced: on return the lane holds the total of value `idx` (NV <= G
-// distinct totals, each held by G / NV lanes).
+// `gl` = lane % G) of NV values per lane (NV a power of two).  The values are
+// scattered while they are reduced: on return the lane holds the totals of
+// values idx .. idx + NOUT - 1, NOUT = max(1, NV / G), in out[]; with NV < G
+// each total is held by G / NV lanes.
+template <int G, int NV> struct Scatter {
+  static constexpr int NOUT = NV > G ? NV / G : 1;  // totals per lane
+  static constexpr int REP = NV >= G ? 1 : G / NV;  // lanes holding each total
+};
 template <int G, int NV>
-__device__ __forceinline__ uint32_t group_scatter_sum(const uint32_t (&v)[NV], int gl, int& idx) {
-  static_assert(NV >= 1 && NV <= G && (NV & (NV - 1)) == 0, "NV: a power of two up to G");
+__device__ __forceinline__ void group_scatter_sum(const uint32_t (&v)[NV], int gl, int& idx,
+                                                  uint32_t (&out)[Scatter<G, NV>::NOUT]) {
+  static_assert(NV >= 1 && NV <= 16 && (NV & (NV - 1)) == 0, "NV: a power of two up to 16");
   uint32_t cur[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) cur[i] = v[i];
@@ -249,7 +256,18 @@ __device__ __forceinline__ uint32_t group_scatter_sum(const uint32_t (&v)[NV], i
     }
   }
   idx = off;
-  return cur[0];
+#pragma unroll
+  for (int i = 0; i < Scatter<G, NV>::NOUT; ++i) out[i] = cur[i];
+}
+
+// The first total index group_scatter_sum leaves with lane gl.
+template <int G, int NV>
+__device__ __forceinline__ int scatter_index(int gl) {
+  int idx = 0;
+#pragma unroll
+  for (int m = G / 2, cnt = NV; m >= 1 && cnt > 1; m >>= 1, cnt >>= 1)
+    if (gl & m) idx += cnt / 2;
+  return idx;
 }
 
 // One float voxel as its two quantisation limbs; tracks max |v| (NaN sticks).
@@ -548,16 +566,17 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
       const int yt = y0 + yl;
       int run_start = za, run_len = 0;
       // image 1 pixel (z, y) of this lane's total: base + z * M (see the emit below)
-      uint32_t* p1 = nullptr;
+      constexpr int NV1 = NL * 2 * BYA;
+      uint32_t* p1[Scatter<GA, NV1>::NOUT];
       {
-        constexpr int NV = NL * 2 * BYA;
-        // the lane's total index depends only on tx (group_scatter_sum)
-        int idx = 0;
+        // the lane's total indices depend only on tx (group_scatter_sum)
+        const int i0 = scatter_index<GA, NV1>(tx);
 #pragma unroll
-        for (int m = GA / 2, cnt = NV; m >= 1 && cnt > 1; m >>= 1, cnt >>= 1)
-          if (tx & m) idx += cnt / 2;
-        const int r = idx % BYA, sl = (idx / BYA) & 1, l = idx / (2 * BYA);
-        p1 = img + set.base[1] + (int64_t)sl * set.F[1] + (yt + r) + l * lstride;
+        for (int j = 0; j < Scatter<GA, NV1>::NOUT; ++j) {
+          const int idx = i0 + j;
+          const int r = idx % BYA, sl = (idx / BYA) & 1, l = idx / (2 * BYA);
+          p1[j] = img + set.base[1] + (int64_t)sl * set.F[1] + (yt + r) + l * lstride;
+        }
       }
       int z = za;
       for (int i = 0; i < nsteps; ++i) {
@@ -628,11 +647,15 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
                 rs[(l * 2 + sl) * BYA + r] = t;
               }
           int idx;
-          const uint32_t tot = group_scatter_sum<GA, NV>(rs, tx, idx);
-          if ((tx & (GA / NV - 1)) == 0) {
-            const int r = idx % BYA, sl = (idx / BYA) & 1, l = idx / (2 * BYA);
-            const int y = yt + r, zz = z + sl;
-            if (y < M && zz < zend && zz < N) red_add_always(p1 + (int64_t)z * M, tot);
+          uint32_t tot[Scatter<GA, NV>::NOUT];
+          group_scatter_sum<GA, NV>(rs, tx, idx, tot);
+          if ((tx & (Scatter<GA, NV>::REP - 1)) == 0) {
+#pragma unroll
+            for (int j = 0; j < Scatter<GA, NV>::NOUT; ++j) {
+              const int r = (idx + j) % BYA, sl = ((idx + j) / BYA) & 1;
+              const int y = yt + r, zz = z + sl;
+              if (y < M && zz < zend && zz < N) red_add_always(p1[j] + (int64_t)z * M, tot[j]);
+            }
           }
         }
         if (++run_len == 8) {
@@ -700,26 +723,25 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
     auto edge_at = [&](int buf, int im, int k, int l, int col) -> uint32_t* {
       return edge + ((((size_t)buf * 2 + im) * 2 + k) * NL + l) * TXc + col;
     };
-    // the edge rows of the z-pair at z (tile x0, y0) into images 5 and 6,
-    // coalesced, by one warp
+    // the edge rows of the z-pair at z (tile x0, y0) into images 5 and 6:
+    // images x 2 rows x NL limbs x TXc columns, shared out over the group's
+    // warps (32 consecutive columns per warp and pass: coalesced)
     auto emit_edges = [&](int buf, int z, int x0, int y0) {
+      constexpr int NIM = (H5 ? 1 : 0) + (H6 ? 1 : 0);
+      constexpr int E = NIM * 2 * NL * TXc;
+      constexpr int PER = (E + 32 * NWG - 1) / (32 * NWG);
 #pragma unroll
-      for (int im = 0; im < 2; ++im) {
-        if ((im == 0 && !H5) || (im == 1 && !H6)) continue;
+      for (int j = 0; j < PER; ++j) {
+        const int e = (j * NWG + bw) * 32 + lane;
+        if (E % (32 * NWG) != 0 && e >= E) continue;
+        const int col = e % TXc;
+        const int l = (e / TXc) % NL;
+        const int k = (e / (TXc * NL)) & 1;
+        const int im = NIM == 2 ? e / (TXc * NL * 2) : (H5 ? 0 : 1);
         const int k5 = im == 0 ? 5 : 6;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int64_t sr = im == 0 ? (int64_t)y0 + z + k : (int64_t)y0 + TYc - 2 + k - z + c6;
-          if (sr < 0 || sr >= set.S[k5]) continue;
-#pragma unroll
-          for (int l = 0; l < NL; ++l)
-#pragma unroll
-            for (int h = 0; h < TXc / 32; ++h) {
-              const int col = lane + 32 * h;
-              if (x0 + col < L)
-                red_add(pix(k5, sr, x0 + col) + l * lstride, *edge_at(buf, im, k, l, col));
-            }
-        }
+        const int64_t sr = im == 0 ? (int64_t)y0 + z + k : (int64_t)y0 + TYc - 2 + k - z + c6;
+        if (sr >= 0 && sr < set.S[k5] && x0 + col < L)
+          red_add(pix(k5, sr, x0 + col) + l * lstride, *edge_at(buf, im, k, l, col));
       }
     };
     // this lane's blocks of the transposed buffer (buffer 0) and of image 0
@@ -742,15 +764,16 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
       const int xt = x0 + xl, yt = y0 + yl;
       int z = za;
       // image 2 pixel (z, x) of this lane's total: base + z * L
-      uint32_t* p2 = nullptr;
+      constexpr int NV2 = NL * 2 * BXB;
+      uint32_t* p2[Scatter<GB, NV2>::NOUT];
       {
-        constexpr int NV = NL * 2 * BXB;
-        int idx = 0;
+        const int i0 = scatter_index<GB, NV2>(gl);
 #pragma unroll
-        for (int m = GB / 2, cnt = NV; m >= 1 && cnt > 1; m >>= 1, cnt >>= 1)
-          if (gl & m) idx += cnt / 2;
-        const int c = idx % BXB, sl = (idx / BXB) & 1, l = idx / (2 * BXB);
-        p2 = img + set.base[2] + (int64_t)sl * set.F[2] + (xt + c) + l * lstride;
+        for (int j = 0; j < Scatter<GB, NV2>::NOUT; ++j) {
+          const int idx = i0 + j;
+          const int c = idx % BXB, sl = (idx / BXB) & 1, l = idx / (2 * BXB);
+          p2[j] = img + set.base[2] + (int64_t)sl * set.F[2] + (xt + c) + l * lstride;
+        }
       }
       for (int i = 0; i < nsteps; ++i) {
         const int buf = s & 1;
@@ -760,8 +783,8 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
           aborted = true;
           break;
         }
-        // the previous z-pair's edge rows (one warp, in turn)
-        if ((H5 || H6) && i > 0 && bw == (s - 1) % NWG) emit_edges(buf ^ 1, z - 2, x0, y0);
+        // the previous z-pair's edge rows
+        if ((H5 || H6) && i > 0) emit_edges(buf ^ 1, z - 2, x0, y0);
         uint32_t v[2][RYB][BXB][NL];
 #pragma unroll
         for (int sl = 0; sl < 2; ++sl)
@@ -835,11 +858,15 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
                 cs[(l * 2 + sl) * BXB + c] = t;
               }
           int idx;
-          const uint32_t tot = group_scatter_sum<GB, NV>(cs, gl, idx);
-          if ((gl & (GB / NV - 1)) == 0) {
-            const int c = idx % BXB, sl = (idx / BXB) & 1, l = idx / (2 * BXB);
-            const int x = xt + c, zz = z + sl;
-            if (x < L && zz < zend && zz < N) red_add_always(p2 + (int64_t)z * L, tot);
+          uint32_t tot[Scatter<GB, NV>::NOUT];
+          group_scatter_sum<GB, NV>(cs, gl, idx, tot);
+          if ((gl & (Scatter<GB, NV>::REP - 1)) == 0) {
+#pragma unroll
+            for (int j = 0; j < Scatter<GB, NV>::NOUT; ++j) {
+              const int c = (idx + j) % BXB, sl = ((idx + j) / BXB) & 1;
+              const int x = xt + c, zz = z + sl;
+              if (x < L && zz < zend && zz < N) red_add_always(p2[j] + (int64_t)z * L, tot[j]);
+            }
           }
         }
         ++s;
@@ -848,7 +875,7 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
       }
       if (aborted) break;
       __syncthreads();  // matches group A's segment-end barrier: edge rows visible
-      if ((H5 || H6) && bw == (s - 1) % NWG) emit_edges((s - 1) & 1, z - 2, x0, y0);
+      if (H5 || H6) emit_edges((s - 1) & 1, z - 2, x0, y0);
       // segment end: windows into the images
       const int zn = z;
 #pragma unroll
