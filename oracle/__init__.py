@@ -11,7 +11,9 @@ The arithmetic lives in ``oracle.c`` (plain C, compiled on first use into
   exact in ``__int128`` for uint8/uint16 volumes, FP64 (compensated) for
   float32 volumes.
 * :func:`project` -- Sec. 3.1, Eq. 4 with Eqs. 5-9 and the +-pi/4 families:
-  the projection images, pixel by pixel.
+  the projection images, pixel by pixel; orders 9 and 10 add the
+  arctan(1/2) image about y and the isometric image (x+z, 2y+x-z) of the
+  further families named after Eq. 9.  Orders up to K = 10.
 * :func:`image_moments` -- Sec. 1, Eq. 1 on one stored image.
 * :func:`central_moments` -- Sec. 4: centroid and central moments from
   their definitions over the voxels (with the matching sums of |.| as the

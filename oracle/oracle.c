@@ -39,9 +39,15 @@
  *   6  (0,1,1)          y-z+(N-1)         x                 M+N-1    L
  *   7  (1,-1,0)         z                 x+y               N        L+M-1
  *   8  (1,1,0)          z                 x-y+(M-1)         N        L+M-1
+ *   9  (2,0,-1)         y                 x+2z              M        L+2N-2
+ *  10  (1,-1,-1)        x+z               2y+x-z+(N-1)      L+N-1    L+2M+N-3
  *
  * Images 0-2 are Eqs. 5-7, images 3-4 are Eqs. 8-9 and images 5-8 are the
- * remaining +-pi/4 projections about the x and z axes (Sec. 3.1).  The signed
+ * remaining +-pi/4 projections about the x and z axes (Sec. 3.1).  Orders
+ * K = 9 and 10 take one more image each from the further families Sec. 3.1
+ * names after Eq. 9: image 9 is the arctan(1/2) rotation about y (line
+ * direction (2,0,-1)), image 10 the isometric projection whose coordinates
+ * (x+z, 2y+x-z) and zero-padded size (L+N-1) x (L+2M+N-3) the paper states.  The signed
  * coordinate of an offset column or row is the stored index minus the
  * offset (the origin shift described in Sec. 5).
  */
@@ -51,6 +57,10 @@
 #include <pthread.h>
 
 typedef __int128 i128;
+
+/* Largest order K the oracle takes, and the image count it needs. */
+#define ORACLE_MAX_K 10
+#define ORACLE_MAX_IMAGES 11
 
 /* ------------------------------------------------------------------ */
 /* moment bookkeeping                                                  */
@@ -95,7 +105,7 @@ static uint32_t load_int(const void* vol, int elem_bytes, int64_t idx) {
 static void* int_worker(void* arg) {
     int_job* J = (int_job*)arg;
     const int K = J->K;
-    i128 xp[9], yp[9], zp[9];
+    i128 xp[ORACLE_MAX_K + 1], yp[ORACLE_MAX_K + 1], zp[ORACLE_MAX_K + 1];
     for (int m = 0; m < J->nmom; ++m) J->acc[m] = 0;
     for (int64_t z = J->z0; z < J->z1; ++z) {
         zp[0] = 1;
@@ -129,12 +139,12 @@ static void* int_worker(void* arg) {
 /*
  * out: nmom little-endian int128 values as (lo, hi) int64 pairs.
  * Returns 0 on success, 1 on bad arguments, 2 if a value overflowed int128.
- * The power tables above are exact in int128 for coordinates < 2^15 and
- * K <= 8 (x^8 < 2^120), which covers every dimension the tests use.
+ * Every product and sum is checked, so a volume whose moments leave the
+ * int128 range (large volumes at K = 9, 10) is reported, never wrapped.
  */
 int oracle_moments_int(const void* vol, int elem_bytes, int64_t L, int64_t M, int64_t N, int K,
                        int nthreads, int64_t* out) {
-    if (!vol || !out || L < 1 || M < 1 || N < 1 || K < 0 || K > 8) return 1;
+    if (!vol || !out || L < 1 || M < 1 || N < 1 || K < 0 || K > ORACLE_MAX_K) return 1;
     if (elem_bytes != 1 && elem_bytes != 2) return 1;
     if (L > 32768 || M > 32768 || N > 32768) return 1;
     if (nthreads < 1) nthreads = 1;
@@ -194,7 +204,7 @@ typedef struct {
 static void* f_worker(void* arg) {
     f_job* J = (f_job*)arg;
     const int K = J->K;
-    double xp[9], yp[9], zp[9];
+    double xp[ORACLE_MAX_K + 1], yp[ORACLE_MAX_K + 1], zp[ORACLE_MAX_K + 1];
     for (int m = 0; m < J->nmom; ++m) J->acc[m] = (nsum){0.0, 0.0};
     for (int64_t z = J->z0; z < J->z1; ++z) {
         zp[0] = 1.0;
@@ -223,7 +233,7 @@ static void* f_worker(void* arg) {
  */
 static int moments_f32_impl(const float* vol, int64_t L, int64_t M, int64_t N, int K,
                             int nthreads, double* out, int abs_values) {
-    if (!vol || !out || L < 1 || M < 1 || N < 1 || K < 0 || K > 8) return 1;
+    if (!vol || !out || L < 1 || M < 1 || N < 1 || K < 0 || K > ORACLE_MAX_K) return 1;
     if (nthreads < 1) nthreads = 1;
     if (nthreads > N) nthreads = (int)N;
     int nmom = oracle_num_moments(K);
@@ -290,6 +300,8 @@ int oracle_image_geometry(int k, int64_t L, int64_t M, int64_t N, int64_t* S, in
         case 6: s = M + N - 1; f = L; os = N - 1; break;
         case 7: s = N; f = L + M - 1; break;
         case 8: s = N; f = L + M - 1; of = M - 1; break;
+        case 9: s = M; f = L + 2 * (N - 1); break;
+        case 10: s = L + N - 1; f = L + 2 * M + N - 3; of = N - 1; break;
         default: return 1;
     }
     *S = s; *F = f; *off_s = os; *off_f = of;
@@ -307,7 +319,9 @@ static void image_coords(int k, int64_t x, int64_t y, int64_t z, int64_t* s, int
         case 5: *s = y + z; *f = x;     break;
         case 6: *s = y - z; *f = x;     break;
         case 7: *s = z;     *f = x + y; break;
-        default: *s = z;    *f = x - y; break;
+        case 8: *s = z;     *f = x - y; break;
+        case 9: *s = y;     *f = x + 2 * z; break;
+        default: *s = x + z; *f = 2 * y + x - z; break;
     }
 }
 
@@ -317,9 +331,10 @@ static void image_coords(int k, int64_t x, int64_t y, int64_t z, int64_t* s, int
  */
 int oracle_project_int(const void* vol, int elem_bytes, int64_t L, int64_t M, int64_t N, int P,
                        uint64_t* out) {
-    if (!vol || !out || L < 1 || M < 1 || N < 1 || P < 1 || P > 9) return 1;
+    if (!vol || !out || L < 1 || M < 1 || N < 1 || P < 1 || P > ORACLE_MAX_IMAGES) return 1;
     if (elem_bytes != 1 && elem_bytes != 2) return 1;
-    int64_t base[9], S[9], F[9], os[9], of[9], tot = 0;
+    int64_t base[ORACLE_MAX_IMAGES], S[ORACLE_MAX_IMAGES], F[ORACLE_MAX_IMAGES];
+    int64_t os[ORACLE_MAX_IMAGES], of[ORACLE_MAX_IMAGES], tot = 0;
     for (int k = 0; k < P; ++k) {
         oracle_image_geometry(k, L, M, N, &S[k], &F[k], &os[k], &of[k]);
         base[k] = tot;
@@ -341,8 +356,9 @@ int oracle_project_int(const void* vol, int elem_bytes, int64_t L, int64_t M, in
 
 /* Same for float32 volumes; each pixel is an FP64 sum. */
 int oracle_project_f32(const float* vol, int64_t L, int64_t M, int64_t N, int P, double* out) {
-    if (!vol || !out || L < 1 || M < 1 || N < 1 || P < 1 || P > 9) return 1;
-    int64_t base[9], S[9], F[9], os[9], of[9], tot = 0;
+    if (!vol || !out || L < 1 || M < 1 || N < 1 || P < 1 || P > ORACLE_MAX_IMAGES) return 1;
+    int64_t base[ORACLE_MAX_IMAGES], S[ORACLE_MAX_IMAGES], F[ORACLE_MAX_IMAGES];
+    int64_t os[ORACLE_MAX_IMAGES], of[ORACLE_MAX_IMAGES], tot = 0;
     for (int k = 0; k < P; ++k) {
         oracle_image_geometry(k, L, M, N, &S[k], &F[k], &os[k], &of[k]);
         base[k] = tot;
@@ -374,9 +390,9 @@ int oracle_project_f32(const float* vol, int64_t L, int64_t M, int64_t N, int P,
  */
 int oracle_image_moments_int(const uint64_t* img, int64_t S, int64_t F, int64_t off_s,
                              int64_t off_f, int K, int64_t* out) {
-    if (!img || !out || S < 1 || F < 1 || K < 0 || K > 8) return 1;
+    if (!img || !out || S < 1 || F < 1 || K < 0 || K > ORACLE_MAX_K) return 1;
     int nm = (K + 1) * (K + 2) / 2;
-    i128 acc[45];
+    i128 acc[(ORACLE_MAX_K + 1) * (ORACLE_MAX_K + 2) / 2];
     for (int m = 0; m < nm; ++m) acc[m] = 0;
     for (int64_t s = 0; s < S; ++s)
         for (int64_t f = 0; f < F; ++f) {
@@ -405,9 +421,9 @@ int oracle_image_moments_int(const uint64_t* img, int64_t S, int64_t F, int64_t 
 /* FP64 version for float images (Neumaier-compensated). */
 int oracle_image_moments_f64(const double* img, int64_t S, int64_t F, int64_t off_s,
                              int64_t off_f, int K, double* out) {
-    if (!img || !out || S < 1 || F < 1 || K < 0 || K > 8) return 1;
+    if (!img || !out || S < 1 || F < 1 || K < 0 || K > ORACLE_MAX_K) return 1;
     int nm = (K + 1) * (K + 2) / 2;
-    nsum acc[45];
+    nsum acc[(ORACLE_MAX_K + 1) * (ORACLE_MAX_K + 2) / 2];
     for (int m = 0; m < nm; ++m) acc[m] = (nsum){0.0, 0.0};
     for (int64_t s = 0; s < S; ++s)
         for (int64_t f = 0; f < F; ++f) {
@@ -443,7 +459,7 @@ int oracle_image_moments_f64(const double* img, int64_t S, int64_t F, int64_t of
  */
 int oracle_central_moments(const void* vol, int elem_bytes, int64_t L, int64_t M, int64_t N,
                            int K, double* centroid, double* mu, double* muabs) {
-    if (!vol || !centroid || !mu || !muabs || L < 1 || M < 1 || N < 1 || K < 0 || K > 8) return 1;
+    if (!vol || !centroid || !mu || !muabs || L < 1 || M < 1 || N < 1 || K < 0 || K > ORACLE_MAX_K) return 1;
     if (elem_bytes != 1 && elem_bytes != 2 && elem_bytes != 4) return 1;
     const int nmom = oracle_num_moments(K);
     int trip[3 * 165];
@@ -485,7 +501,7 @@ int oracle_central_moments(const void* vol, int elem_bytes, int64_t L, int64_t M
     nsum* acc = (nsum*)calloc((size_t)nmom, sizeof(nsum));
     nsum* aab = (nsum*)calloc((size_t)nmom, sizeof(nsum));
     if (!acc || !aab) { free(acc); free(aab); return 1; }
-    double xp[9], yp[9], zp[9];
+    double xp[ORACLE_MAX_K + 1], yp[ORACLE_MAX_K + 1], zp[ORACLE_MAX_K + 1];
     for (int64_t z = 0; z < N; ++z) {
         zp[0] = 1.0;
         for (int e = 1; e <= K; ++e) zp[e] = zp[e - 1] * ((double)z - c[2]);

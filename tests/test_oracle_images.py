@@ -30,6 +30,8 @@ FORMS = {
     6: ((0, 1, -1), (1, 0, 0)),
     7: ((0, 0, 1), (1, 1, 0)),
     8: ((0, 0, 1), (1, -1, 0)),
+    9: ((0, 1, 0), (1, 0, 2)),     # arctan(1/2) about y
+    10: ((1, 0, 1), (1, 2, -1)),   # isometric: (x+z, 2y+x-z)
 }
 
 
@@ -48,10 +50,13 @@ def test_image_sizes():
         3: (M, L + N - 1), 4: (M, L + N - 1),     # Eqs. 8-9: (L+N-1) x M
         5: (M + N - 1, L), 6: (M + N - 1, L),
         7: (N, L + M - 1), 8: (N, L + M - 1),
+        9: (M, L + 2 * N - 2),
+        10: (L + N - 1, L + 2 * M + N - 3),       # the paper's zero-padded isometric size
     }
     for k, (S, F) in want.items():
         assert oracle.image_geometry(k, L, M, N)[:2] == (S, F)
-    assert [oracle.num_images(K) for K in (0, 1, 2, 3, 4, 6, 8)] == [3, 3, 3, 4, 5, 7, 9]
+    assert [oracle.num_images(K) for K in (0, 1, 2, 3, 4, 6, 8, 9, 10)] == [
+        3, 3, 3, 4, 5, 7, 9, 10, 11]
 
 
 @pytest.mark.parametrize("pos", [(0, 0, 0), (6, 4, 2), (6, 0, 2), (0, 4, 0), (3, 2, 1)])
@@ -60,8 +65,8 @@ def test_single_voxel_lands_on_predicted_pixel(pos):
     x, y, z = pos
     vol = np.zeros((N, M, L), dtype=np.uint8)
     vol[z, y, x] = 9
-    imgs = oracle.project(vol, 9)
-    for k in range(9):
+    imgs = oracle.project(vol, 11)
+    for k in range(11):
         S, F, os_, of = oracle.image_geometry(k, L, M, N)
         (sa, sb, sc), (fa, fb, fc) = FORMS[k]
         s = sa * x + sb * y + sc * z + os_
@@ -74,10 +79,10 @@ def test_single_voxel_lands_on_predicted_pixel(pos):
 def test_mass_conservation():
     vol = synth.uniform_volume((6, 5, 8), np.uint16, seed=1)
     tot = int(vol.astype(np.uint64).sum())
-    for im in oracle.project(vol, 9):
+    for im in oracle.project(vol, 11):
         assert int(im.sum()) == tot
     fvol = synth.uniform_volume((6, 5, 8), np.float32, seed=1)
-    for im in oracle.project(fvol, 9):
+    for im in oracle.project(fvol, 11):
         assert im.sum() == pytest.approx(float(fvol.astype(np.float64).sum()), rel=1e-13)
 
 
@@ -210,3 +215,77 @@ def test_float_image_moments_exact():
         mag = sum(Fraction(float(img[s, f])) * abs(s - 2) ** a * abs(f - 3) ** b
                   for s in range(5) for f in range(6))
         assert abs(Fraction(t) - exact) <= Fraction(1e-14) * mag
+
+
+def test_brute_force_images_9_and_10():
+    """Images 9 and 10 pixel by pixel from a pure-Python loop over the voxels."""
+    vol = synth.uniform_volume((4, 3, 5), np.uint16, seed=7)
+    N, M, L = vol.shape
+    imgs = oracle.project(vol, 11)
+    for k in (9, 10):
+        S, F, os_, of = oracle.image_geometry(k, L, M, N)
+        want = np.zeros((S, F), dtype=np.uint64)
+        (sa, sb, sc), (fa, fb, fc) = FORMS[k]
+        for z in range(N):
+            for y in range(M):
+                for x in range(L):
+                    want[sa * x + sb * y + sc * z + os_, fa * x + fb * y + fc * z + of] += int(vol[z, y, x])
+        np.testing.assert_array_equal(imgs[k], want)
+
+
+def test_image_moments_expand_to_3d_moments_k10():
+    """Images 9 and 10 at order 10: every 2-D moment is the multinomial
+    expansion of the 3-D moments."""
+    vol = synth.uniform_volume((3, 4, 5), np.uint8, seed=5)
+    N, M, L = vol.shape
+    K = 10
+    m3 = oracle.moments(vol, K)
+    I = {t: i for i, t in enumerate(oracle.graded_triples(K))}
+    imgs = oracle.project(vol, 11)
+    geo = [oracle.image_geometry(k, L, M, N) for k in range(11)]
+    for k in (0, 4, 9, 10):
+        for n in range(K + 1):
+            for a in range(n, -1, -1):
+                want = sum(c * m3[I[e]] for e, c in expand(*FORMS[k], a, n - a).items())
+                assert img_moment(imgs, geo, k, a, n - a, K) == want, (k, a, n - a)
+
+
+def exact_rank(rows):
+    """Rank over the rationals (fraction-exact Gaussian elimination)."""
+    A = [[Fraction(v) for v in r] for r in rows]
+    rank, col = 0, 0
+    ncol = len(A[0]) if A else 0
+    while rank < len(A) and col < ncol:
+        piv = next((i for i in range(rank, len(A)) if A[i][col] != 0), None)
+        if piv is None:
+            col += 1
+            continue
+        A[rank], A[piv] = A[piv], A[rank]
+        for i in range(rank + 1, len(A)):
+            f = A[i][col] / A[rank][col]
+            if f:
+                A[i] = [a - f * b for a, b in zip(A[i], A[rank])]
+        rank += 1
+        col += 1
+    return rank
+
+
+@pytest.mark.parametrize("K", [8, 9, 10])
+def test_images_reach_full_rank(K):
+    """The rank argument: the 2-D moments of degree n of images 0..K span all
+    (n+1)(n+2)/2 monomials of degree n, for every n <= K, so the 3-D moments
+    follow from the images (and K images would not be enough at n = K)."""
+    P = oracle.num_images(K)
+    for n in range(K + 1):
+        monos = [(p, q, n - p - q) for p in range(n, -1, -1) for q in range(n - p, -1, -1)]
+        rows = []
+        for k in range(P):
+            for a in range(n, -1, -1):
+                e = expand(*FORMS[k], a, n - a)
+                rows.append([e.get(m, 0) for m in monos])
+        assert exact_rank(rows) == len(monos), (K, n)
+    n = K
+    monos = [(p, q, n - p - q) for p in range(n, -1, -1) for q in range(n - p, -1, -1)]
+    rows = [[expand(*FORMS[k], a, n - a).get(m, 0) for m in monos]
+            for k in range(P - 1) for a in range(n, -1, -1)]
+    assert exact_rank(rows) < len(monos)

@@ -63,7 +63,7 @@ def idx(K):
 
 def test_faulhaber_reference_itself():
     # the closed form against direct sums (pins the pin)
-    for p in range(9):
+    for p in range(11):
         for n in (1, 2, 7, 30):
             assert faulhaber(p, n) == sum(t ** p for t in range(n))
 
@@ -231,7 +231,7 @@ def test_int128_overflow_is_detected():
 
 def test_bad_arguments_rejected():
     with pytest.raises(ValueError):
-        oracle.moments(np.zeros((2, 2, 2), np.uint8), 9)
+        oracle.moments(np.zeros((2, 2, 2), np.uint8), 11)
     with pytest.raises(TypeError):
         oracle.moments(np.zeros((2, 2, 2), np.int32), 3)
 
@@ -248,3 +248,47 @@ def test_golden_small_volumes():
         vol = synth.uniform_volume(tuple(c["shape_zyx"]), dt, seed=c["seed"])
         assert oracle.moments(vol, c["K"]) == [int(v) for v in c["moments"]]
         assert brute_moments(vol, min(c["K"], 3)) == [int(v) for v in c["moments"]][:oracle.num_moments(min(c["K"], 3))]
+
+
+# ----------------------------------------------------------------------
+# orders 9 and 10
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (5, 7, 3), (16, 9, 33)])
+def test_constant_box_closed_form_k10(shape):
+    N, M, L = shape
+    vol = np.full(shape, 65535, dtype=np.uint16)
+    got = oracle.moments(vol, 10, nthreads=3)
+    for (p, q, r), g in zip(oracle.graded_triples(10), got):
+        assert g == 65535 * faulhaber(p, L) * faulhaber(q, M) * faulhaber(r, N), (p, q, r)
+
+
+@pytest.mark.parametrize("pos", [(0, 0, 0), (12, 9, 7), (5, 3, 2)])
+def test_single_voxel_k10(pos):
+    x0, y0, z0 = pos
+    vol = np.zeros((8, 10, 13), dtype=np.uint8)
+    vol[z0, y0, x0] = 251
+    got = oracle.moments(vol, 10, nthreads=2)
+    for (p, q, r), g in zip(oracle.graded_triples(10), got):
+        assert g == 251 * x0 ** p * y0 ** q * z0 ** r
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_brute_force_k10(seed):
+    vol = synth.uniform_volume((3, 4, 5), np.uint16, seed=300 + seed)
+    assert oracle.moments(vol, 10, nthreads=2) == brute_moments(vol, 10)
+
+
+def test_float_k10_against_exact_rationals():
+    vol = synth.uniform_volume((3, 4, 5), np.float32, 41, low=-2.0, high=3.0)
+    got = oracle.moments(vol, 10)
+    for g, w in zip(got, brute_moments(vol, 10)):
+        assert g == pytest.approx(float(w), rel=1e-12, abs=1e-9)
+
+
+def test_int128_overflow_is_detected_k10():
+    vol = np.zeros((1, 1, 8192), dtype=np.uint16)
+    vol[0, 0, 8191] = 65535  # 65535 * 8191^9 > 2^127 > 65535 * 8191^8
+    with pytest.raises(OverflowError):
+        oracle.moments(vol, 9)
+    assert oracle.moments(vol, 8)[oracle.graded_triples(8).index((8, 0, 0))] == 65535 * 8191 ** 8
