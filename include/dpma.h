@@ -39,6 +39,11 @@
  *     6  (0,1,1)     y-z+(N-1)   x             M+N-1    L        (Sec. 3.1)
  *     7  (1,-1,0)    z           x+y           N        L+M-1    +-pi/4 about z
  *     8  (1,1,0)     z           x-y+(M-1)     N        L+M-1    (Sec. 3.1)
+ *     9  (2,0,-1)    y           x+2z          M        L+2N-2   arctan(1/2) about y
+ *    10  (1,-1,-1)   x+z         2y+x-z+(N-1)  L+N-1    L+2M+N-3 isometric (Sec. 3.1)
+ *
+ *   Order K uses images 0..max(2, K); images 9 and 10 (orders 9 and 10)
+ *   are taken for integer volumes only.
  *
  *   Integer volumes: uint32 pixels (exact: dimensions are capped at 65536,
  *   so a line sum of uint16 voxels stays below 2^32).  Float32 volumes:
@@ -71,7 +76,7 @@ extern "C" {
 
 typedef enum dpma_status {
   DPMA_OK = 0,
-  DPMA_ERR_INVALID_ARG = 1, /* null pointer, dimension < 1 or > 65536, K outside 0..8, bad dtype */
+  DPMA_ERR_INVALID_ARG = 1, /* null pointer, dimension < 1 or > 65536, K out of range, bad dtype */
   DPMA_ERR_OVERFLOW = 2,    /* an exact intermediate could exceed the int128 range */
   DPMA_ERR_OOM = 3,         /* device memory allocation failed */
   DPMA_ERR_CUDA = 4,        /* a CUDA runtime call failed; see dpma_last_error() */
@@ -82,7 +87,14 @@ typedef enum dpma_status {
 
 typedef enum dpma_dtype { DPMA_U8 = 0, DPMA_U16 = 1, DPMA_F32 = 2 } dpma_dtype;
 
-#define DPMA_MAX_K 8
+/* Largest order K: 10 for uint8/uint16 volumes through the single-volume
+ * entry points (dpma_moments, _async, _host, dpma_project,
+ * dpma_image_moments, dpma_combine, dpma_moments_from_projections,
+ * dpma_derived_moments); 8 for float32 volumes and for the batched
+ * launches, the server and dpma_moments_noalloc. */
+#define DPMA_MAX_K 10
+#define DPMA_MAX_K_FLOAT 8
+#define DPMA_MAX_K_BATCH 8
 #define DPMA_MAX_DIM 65536
 
 /* ---------------- helpers (host only, no GPU needed) ---------------- */
@@ -91,7 +103,7 @@ typedef enum dpma_dtype { DPMA_U8 = 0, DPMA_U16 = 1, DPMA_F32 = 2 } dpma_dtype;
 int dpma_num_moments(int K);
 /* Number of projection images the method uses for order K: max(3, K+1). */
 int dpma_num_images(int K);
-/* Position of M_pqr in graded order; -1 if p, q or r is negative or p+q+r > 8. */
+/* Position of M_pqr in graded order; -1 if p, q or r is negative or p+q+r > DPMA_MAX_K. */
 int dpma_moment_index(int p, int q, int r);
 /* Static text for a status code. */
 const char* dpma_status_string(dpma_status s);
@@ -113,7 +125,7 @@ int dpma_last_float_path(void);
  * Copies already issued still land before a CTA leaves.  Process-wide.
  */
 dpma_status dpma_set_wait_budget(int64_t cycles);
-/* Geometry of image k (0..8) of an L x M x N volume (table above). */
+/* Geometry of image k (0..10) of an L x M x N volume (table above). */
 dpma_status dpma_image_geometry(int k, int64_t L, int64_t M, int64_t N, int64_t* S, int64_t* F,
                                 int64_t* off_s, int64_t* off_f);
 /* Bytes of the image buffer dpma_project writes (all P images, layout above). */

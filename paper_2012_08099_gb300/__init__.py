@@ -181,9 +181,9 @@ def combine_plan(K: int, n: int):
     """(D, img, a, C) of the exact degree-n combine for order K."""
     nm = ctypes.c_int()
     D = ctypes.c_int64()
-    img = (ctypes.c_int32 * 45)()
-    a = (ctypes.c_int32 * 45)()
-    C = (ctypes.c_int64 * (45 * 45))()
+    img = (ctypes.c_int32 * 66)()
+    a = (ctypes.c_int32 * 66)()
+    C = (ctypes.c_int64 * (66 * 66))()
     _check(lib().dpma_combine_plan(K, n, ctypes.byref(nm), ctypes.byref(D), img, a, C))
     m = nm.value
     Cm = np.array(C[: m * m], dtype=np.int64).reshape(m, m)
@@ -238,7 +238,7 @@ def moments(volume, K: int, dtype: int | None = None, out=None):
     L, M, N = _shape(volume)
     nm = lib().dpma_num_moments(K)
     if nm == 0:
-        raise DpmaError(1, "K must lie in 0..8")
+        raise DpmaError(1, "K must lie in 0..10")
     if out is None:
         out = torch.empty((nm, 2) if dt != F32 else (nm,),
                           dtype=torch.int64 if dt != F32 else torch.float64, device=volume.device)

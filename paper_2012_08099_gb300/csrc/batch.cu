@@ -46,7 +46,7 @@ using dpma::batch::BTask;
 namespace {
 
 // the 2-D moments T_ab of every image of the volume being reduced (int128)
-constexpr int kPartBytes = kMaxImages * kMax2D * 16;
+constexpr int kPartBytes = kMaxImagesBatch * kMax2DBatch * 16;
 constexpr int kSlabWords = 6144;  // one stage buffer (24 KB), double-buffered
 // stage buffers of a one-CTA-per-SM launch whose images leave room (48 KB):
 // half as many stages, so half as many stage barriers
@@ -754,7 +754,7 @@ cudaError_t plans_for_device(const DevPlans** out) {
   DevPlans& dp = g_plans[dev];
   if (!dp.words) {
     std::vector<int64_t> words;
-    for (int K = 0; K <= kMaxK; ++K) {
+    for (int K = 0; K <= kMaxKBatch; ++K) {
       std::vector<int64_t> w(8192);
       int off[kMaxK + 1];
       const size_t n = pack_combine_plan(K, w.data(), w.size(), off);
@@ -1102,8 +1102,9 @@ dpma_status validate(const dpma_volume_desc* descs, int count) {
     if (!d.volume) return bfail(DPMA_ERR_INVALID_ARG, at + "null volume");
     if (d.out_offset < 0 || d.out_offset % 16 != 0)
       return bfail(DPMA_ERR_INVALID_ARG, at + "out_offset must be a non-negative multiple of 16");
-    if (dpma_workspace_size(d.L, d.M, d.N, (dpma_dtype)d.dtype, d.K) == 0)
-      return bfail(DPMA_ERR_INVALID_ARG, at + "bad dimensions, dtype or K");
+    if (d.K > DPMA_MAX_K_BATCH ||
+        dpma_workspace_size(d.L, d.M, d.N, (dpma_dtype)d.dtype, d.K) == 0)
+      return bfail(DPMA_ERR_INVALID_ARG, at + "bad dimensions, dtype or K (batches: K <= 8)");
     if (d.dtype != DPMA_F32) {
       const double vmax = d.dtype == DPMA_U8 ? 255.0 : 65535.0;
       if (log2_bound_2d(d.L, d.M, d.N, vmax, d.K) > 125.0 ||

@@ -53,9 +53,10 @@ bool is_float(dpma_dtype d) { return d == DPMA_F32; }
 dpma_status check_args(int64_t L, int64_t M, int64_t N, dpma_dtype dtype, int K) {
   if (L < 1 || M < 1 || N < 1 || L > DPMA_MAX_DIM || M > DPMA_MAX_DIM || N > DPMA_MAX_DIM)
     return fail(DPMA_ERR_INVALID_ARG, "dimensions must lie in 1..65536");
-  if (K < 0 || K > DPMA_MAX_K) return fail(DPMA_ERR_INVALID_ARG, "K must lie in 0..8");
   if (dtype != DPMA_U8 && dtype != DPMA_U16 && dtype != DPMA_F32)
     return fail(DPMA_ERR_INVALID_ARG, "unknown dtype");
+  if (K < 0 || K > (dtype == DPMA_F32 ? DPMA_MAX_K_FLOAT : DPMA_MAX_K))
+    return fail(DPMA_ERR_INVALID_ARG, "K must lie in 0..10 (0..8 for float32)");
   if (dtype == DPMA_F32) {
     // float-float coordinate powers must stay well inside the float range
     const double maxc = (double)(L + M + N);
@@ -449,7 +450,7 @@ size_t dpma_workspace_size(int64_t L, int64_t M, int64_t N, dpma_dtype dtype, in
 dpma_status dpma_combine_plan(int K, int n, int* nmono, int64_t* D, int32_t* img, int32_t* a,
                               int64_t* C) {
   if (K < 0 || K > DPMA_MAX_K || n < 0 || n > K)
-    return fail(DPMA_ERR_INVALID_ARG, "need 0 <= n <= K <= 8");
+    return fail(DPMA_ERR_INVALID_ARG, "need 0 <= n <= K <= 10");
   const CombinePlan* cp = combine_plan(K);
   if (!cp) return fail(DPMA_ERR_INTERNAL, "combine plan failed its exact check");
   const DegreePlan& d = cp->deg[n];
@@ -624,9 +625,10 @@ dpma_status dpma_image_moments(const void* images, int64_t L, int64_t M, int64_t
 dpma_status dpma_combine(const void* moments2d, dpma_dtype dtype, int K, void* out, void* stream,
                          int* status) {
   if (!moments2d || !out) return fail(DPMA_ERR_INVALID_ARG, "null pointer");
-  if (K < 0 || K > DPMA_MAX_K) return fail(DPMA_ERR_INVALID_ARG, "K must lie in 0..8");
   if (dtype != DPMA_U8 && dtype != DPMA_U16 && dtype != DPMA_F32)
     return fail(DPMA_ERR_INVALID_ARG, "unknown dtype");
+  if (K < 0 || K > (dtype == DPMA_F32 ? DPMA_MAX_K_FLOAT : DPMA_MAX_K))
+    return fail(DPMA_ERR_INVALID_ARG, "K must lie in 0..10 (0..8 for float32)");
   cudaError_t e = prepare_combine(K);
   if (e != cudaSuccess) return cuda_fail(e, "combine plan");
   e = launch_combine(moments2d, K, is_float(dtype), out, status, static_cast<cudaStream_t>(stream));

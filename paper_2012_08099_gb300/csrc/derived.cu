@@ -164,7 +164,7 @@ extern "C" dpma_status dpma_derived_moments(const void* moments, dpma_dtype dtyp
     return DPMA_ERR_INVALID_ARG;
   }
   if (K < 0 || K > DPMA_MAX_K || (dtype != DPMA_U8 && dtype != DPMA_U16 && dtype != DPMA_F32)) {
-    set_last_error("K must lie in 0..8 and dtype be a library dtype");
+    set_last_error("K must lie in 0..10 and dtype be a library dtype");
     return DPMA_ERR_INVALID_ARG;
   }
   DerivedParams d{};

@@ -108,7 +108,10 @@ cudaError_t launch_clear(void* p, size_t bytes, int* status, cudaStream_t st,
                          const int* gate = nullptr);
 
 // Step 1: images must be zeroed by the caller (the launcher does not clear).
+// Orders 9 and 10 (integer volumes) add images 9 and 10 in a second kernel.
 cudaError_t launch_project(const ProjectArgs& a, cudaStream_t st);
+// Images 9 and 10 of an integer volume (nothing if a.set.P <= 9).
+cudaError_t launch_project_extra(const ProjectArgs& a, cudaStream_t st);
 
 // Step 1 on integer lanes (k1_int.cuh): uint32 images for integer volumes;
 // for float32 volumes two sets of int32 images, one per quantisation limb

@@ -30,6 +30,14 @@ cudaError_t launch_f32_hi(int P, const ProjectArgs& a, cudaStream_t st);
 }  // namespace k1
 
 cudaError_t launch_project(const ProjectArgs& a, cudaStream_t st) {
+  if (a.set.P > 9) {
+    // orders 9 and 10: images 0-8 in the fused pass, images 9 and 10 beside it
+    ProjectArgs b = a;
+    b.set.P = 9;
+    cudaError_t e = launch_project(b, st);
+    if (e != cudaSuccess) return e;
+    return launch_project_extra(a, st);
+  }
   const int P = a.set.P;
   if (P < 3 || P > 9) return cudaErrorInvalidValue;
   const bool hi = P >= 6;

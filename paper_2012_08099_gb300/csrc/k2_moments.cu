@@ -388,6 +388,14 @@ cudaError_t launch_k2(const void* images, const ImageSet& set, int K, bool is_fl
     DPMA_K2_CASE(0) DPMA_K2_CASE(1) DPMA_K2_CASE(2) DPMA_K2_CASE(3) DPMA_K2_CASE(4)
     DPMA_K2_CASE(5) DPMA_K2_CASE(6) DPMA_K2_CASE(7) DPMA_K2_CASE(8)
 #undef DPMA_K2_CASE
+#define DPMA_K2_INT_CASE(k)                                                          \
+  case k:                                                                            \
+    if (is_float) return cudaErrorInvalidValue;                                      \
+    if (sgn) k2_int_cascade_kernel<k, true><<<g, kUnitThreads, 0, st>>>(p);          \
+    else k2_int_cascade_kernel<k, false><<<g, kUnitThreads, 0, st>>>(p);             \
+    break;
+    DPMA_K2_INT_CASE(9) DPMA_K2_INT_CASE(10)
+#undef DPMA_K2_INT_CASE
     default: return cudaErrorInvalidValue;
   }
   cudaError_t e = cudaGetLastError();

@@ -97,7 +97,7 @@ extern "C" dpma_status dpma_moments_noalloc(const void* volume, int64_t L, int64
   if (!volume || !out) return fail_with(DPMA_ERR_INVALID_ARG, "null volume or output pointer");
   if (L < 1 || M < 1 || N < 1 || L > DPMA_MAX_DIM || M > DPMA_MAX_DIM || N > DPMA_MAX_DIM)
     return fail_with(DPMA_ERR_INVALID_ARG, "dimensions must lie in 1..65536");
-  if (K < 0 || K > DPMA_MAX_K) return fail_with(DPMA_ERR_INVALID_ARG, "K must lie in 0..8");
+  if (K < 0 || K > DPMA_MAX_K_BATCH) return fail_with(DPMA_ERR_INVALID_ARG, "K must lie in 0..8");
   if (dtype != DPMA_U8 && dtype != DPMA_U16 && dtype != DPMA_F32)
     return fail_with(DPMA_ERR_INVALID_ARG, "unknown dtype");
   const bool fl = dtype == DPMA_F32;
@@ -145,7 +145,7 @@ extern "C" dpma_status dpma_moments_noalloc(const void* volume, int64_t L, int64
       fresh.plans = static_cast<int64_t*>(ptr);
       std::vector<int64_t> words;
       std::vector<int64_t> buf(8192);
-      for (int k = 0; k <= kMaxK; ++k) {
+      for (int k = 0; k <= kMaxKBatch; ++k) {
         int off[kMaxK + 1];
         const size_t nw = pack_combine_plan(k, buf.data(), buf.size(), off);
         if (nw == 0) return fail_with(DPMA_ERR_INTERNAL, "combine plan unavailable");

@@ -1,5 +1,5 @@
 // Exact combine plan for the final step of the Discrete Projection Moment
-// method (Sec. 3.2, Eqs. 10-16, generalised to any order K <= 8).
+// method (Sec. 3.2, Eqs. 10-16, generalised to any order K <= 10).
 //
 // An image with forms (u, w) has 2-D moments
 //     T_ab = sum_voxels V (u.x)^a (w.x)^b,
@@ -8,7 +8,9 @@
 // n, the rows of every image's (a, n-a) expansions gives an integer system
 // A_n m_n = t_n; K+1 distinct line directions give it full column rank for
 // every n <= K (the axis family of Eqs. 5-7 plus the +-pi/4 family named
-// after Eq. 9 hold 9 directions, enough for K <= 8).  The plan keeps, in a
+// after Eq. 9 hold 9 directions, enough for K <= 8; the arctan(1/2) image
+// about y and the isometric image of the further families extend it to
+// K = 10).  The plan keeps, in a
 // fixed order, the rows that raise the rank, inverts the square system
 // exactly and stores it as an integer matrix C over a common denominator D:
 //     m_n = (1/D) C t_sel.
@@ -223,6 +225,8 @@ bool image_geom(int k, int64_t L, int64_t M, int64_t N, ImageGeom* g) {
       {{0, 1, -1}, {1, 0, 0}},  // 6: (y-z, x)
       {{0, 0, 1}, {1, 1, 0}},   // 7: (x+y, z)   +-pi/4 about z
       {{0, 0, 1}, {1, -1, 0}},  // 8: (x-y, z)
+      {{0, 1, 0}, {1, 0, 2}},   // 9: (x+2z, y)  arctan(1/2) about y, line (2,0,-1)
+      {{1, 0, 1}, {1, 2, -1}},  // 10: isometric (x+z, 2y+x-z), line (1,-1,-1)
   };
   if (k < 0 || k >= kMaxImages) return false;
   std::memcpy(g->slow, forms[k][0], sizeof(g->slow));

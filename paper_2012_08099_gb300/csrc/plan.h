@@ -6,14 +6,23 @@
 
 namespace dpma {
 
-constexpr int kMaxK = 8;
-constexpr int kMaxImages = 9;
-constexpr int kMaxMono = 45;            // (8+1)(8+2)/2 monomials of degree 8
-constexpr int kMax2D = 45;              // 2-D moments a+b <= 8 per image
+// Single-volume pipeline: integer volumes up to order 10 (11 images: the
+// axis and +-pi/4 families plus the arctan(1/2) and isometric images),
+// float32 volumes up to order 8.
+constexpr int kMaxK = 10;
+constexpr int kMaxKFloat = 8;
+constexpr int kMaxImages = 11;
+constexpr int kMaxMono = 66;            // (10+1)(10+2)/2 monomials of degree 10
+constexpr int kMax2D = 66;              // 2-D moments a+b <= 10 per image
+// Batched launches, the server and the allocation-free entry: order <= 8.
+constexpr int kMaxKBatch = 8;
+constexpr int kMaxImagesBatch = 9;
+constexpr int kMax2DBatch = 45;
 
 // Linear forms of one projection image: the voxel (x,y,z) lands on row
 // s = slow.(x,y,z) + off_s and column f = fast.(x,y,z) + off_f of an
-// [S][F] row-major image (Sec. 3.1, Eq. 4; Eqs. 5-9 and the +-pi/4 families).
+// [S][F] row-major image (Sec. 3.1, Eq. 4; Eqs. 5-9, the +-pi/4 families and,
+// for orders 9 and 10, the arctan(1/2) image about y and the isometric image).
 struct ImageGeom {
   int slow[3];
   int fast[3];

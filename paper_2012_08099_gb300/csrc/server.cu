@@ -720,7 +720,7 @@ dpma_status dpma_server_create(const dpma_server_config* cfg, dpma_server** out)
     s->streams.push_back(st);
   }
   // every plan resident before serving starts: nothing synchronises later
-  for (int K = 0; K <= DPMA_MAX_K && e == cudaSuccess; ++K) e = prepare_combine(K);
+  for (int K = 0; K <= DPMA_MAX_K_BATCH && e == cudaSuccess; ++K) e = prepare_combine(K);
   if (e == cudaSuccess) e = batch::prepare_plans();
   if (e != cudaSuccess) {
     for (cudaStream_t st : s->streams) cudaStreamDestroy(st);

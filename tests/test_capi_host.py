@@ -27,6 +27,7 @@ FORMS = {
     0: ((0, 1, 0), (1, 0, 0)), 1: ((0, 0, 1), (0, 1, 0)), 2: ((0, 0, 1), (1, 0, 0)),
     3: ((0, 1, 0), (1, 0, 1)), 4: ((0, 1, 0), (1, 0, -1)), 5: ((0, 1, 1), (1, 0, 0)),
     6: ((0, 1, -1), (1, 0, 0)), 7: ((0, 0, 1), (1, 1, 0)), 8: ((0, 0, 1), (1, -1, 0)),
+    9: ((0, 1, 0), (1, 0, 2)), 10: ((1, 0, 1), (1, 2, -1)),
 }
 
 
@@ -52,32 +53,33 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_moment_order_matches_oracle(lib):
-    for K in range(9):
+    for K in range(11):
         assert dpma.num_moments(K) == oracle.num_moments(K)
         assert dpma.num_images(K) == oracle.num_images(K)
         for i, (p, q, r) in enumerate(oracle.graded_triples(K)):
             assert dpma.moment_index(p, q, r) == i
-    assert dpma.num_moments(9) == 0 and dpma.num_moments(-1) == 0
-    assert dpma.moment_index(5, 4, 0) == -1 and dpma.moment_index(-1, 0, 0) == -1
+    assert dpma.num_moments(11) == 0 and dpma.num_moments(-1) == 0
+    assert dpma.moment_index(6, 5, 0) == -1 and dpma.moment_index(-1, 0, 0) == -1
 
 
 @pytest.mark.parametrize("dims", [(1, 1, 1), (7, 5, 3), (64, 64, 64), (512, 300, 17)])
 def test_image_geometry_matches_oracle(lib, dims):
     L, M, N = dims
-    for k in range(9):
+    for k in range(11):
         assert dpma.image_geometry(k, L, M, N) == oracle.image_geometry(k, L, M, N)
 
 
 def test_buffer_sizes(lib):
     L, M, N = 37, 21, 13
     for dt, per in ((dpma.U8, 4), (dpma.U16, 4), (dpma.F32, 8)):
-        for K in (0, 3, 6, 8):
+        for K in (0, 3, 6, 8) + ((9, 10) if dt != dpma.F32 else ()):
             want = sum(oracle.image_geometry(k, L, M, N)[0] * oracle.image_geometry(k, L, M, N)[1]
                        for k in range(oracle.num_images(K))) * per
             assert dpma.images_size(L, M, N, dt, K) == want
             assert dpma.workspace_size(L, M, N, dt, K) > want
     assert dpma.images_size(0, 5, 5, dpma.U8, 3) == 0
-    assert dpma.workspace_size(5, 5, 5, dpma.U8, 9) == 0
+    assert dpma.workspace_size(5, 5, 5, dpma.U8, 11) == 0
+    assert dpma.workspace_size(5, 5, 5, dpma.F32, 9) == 0  # float32 volumes: K <= 8
 
 
 def expand(fs, ff, a, b, n):
@@ -96,7 +98,7 @@ def expand(fs, ff, a, b, n):
     return [poly.get(m, 0) for m in monos]
 
 
-@pytest.mark.parametrize("K", [0, 1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("K", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
 def test_combine_plan_is_an_exact_inverse(lib, K):
     for n in range(K + 1):
         D, img, a, C = dpma.combine_plan(K, n)
@@ -119,6 +121,9 @@ def test_combine_denominators():
     # small integer matrices: |C| <= 2100 at K = 8, 120 at K = 6
     assert max(abs(int(v)) for n in range(9) for v in dpma.combine_plan(8, n)[3].ravel()) == 2100
     assert max(abs(int(v)) for n in range(7) for v in dpma.combine_plan(6, n)[3].ravel()) == 120
+    # orders 9 and 10 (with the arctan(1/2) and isometric images)
+    assert [dpma.combine_plan(10, n)[0] for n in range(11)][:9] == want
+    assert dpma.combine_plan(9, 9)[0] == dpma.combine_plan(10, 9)[0]
 
 
 def test_k_plus_one_directions_are_needed():
@@ -143,7 +148,7 @@ def test_k_plus_one_directions_are_needed():
             col += 1
         return rk
 
-    for n in (3, 4, 6):
+    for n in (3, 4, 6, 9, 10):
         nm = (n + 1) * (n + 2) // 2
         full = [expand(*FORMS[k], a, n - a, n) for k in range(n + 1) for a in range(n, -1, -1)]
         short = [expand(*FORMS[k], a, n - a, n) for k in range(n) for a in range(n, -1, -1)]
@@ -151,7 +156,8 @@ def test_k_plus_one_directions_are_needed():
         assert rank(short) < nm
 
 
-@pytest.mark.parametrize("K,dtype", [(3, np.uint8), (4, np.uint16), (6, np.uint16), (8, np.uint8)])
+@pytest.mark.parametrize("K,dtype", [(3, np.uint8), (4, np.uint16), (6, np.uint16), (8, np.uint8),
+                                     (9, np.uint16), (10, np.uint8)])
 def test_plan_applied_to_oracle_image_moments_gives_oracle_moments(K, dtype):
     vol = synth.uniform_volume((5, 6, 7), dtype, seed=K)
     N, M, L = vol.shape

@@ -222,7 +222,7 @@ def test_z_slab_additivity_at_full_size(dpma):
 def test_invalid_arguments(dpma):
     t = torch.zeros((4, 4, 4), dtype=torch.uint8, device="cuda")
     with pytest.raises(dpma.DpmaError) as e:
-        dpma.moments(t, 9)
+        dpma.moments(t, 11)
     assert e.value.status == 1
     big = torch.zeros((1, 1, 1), dtype=torch.int16, device="cuda")
     # 65536^3 voxels of uint16 at K=8 would overflow int128: refused before launch
