@@ -319,6 +319,28 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
     // the staging buffer is rewritten only after all earlier work on st
     e = cudaEventRecord(ev, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(copy_st, ev, 0);
+    if (e == cudaSuccess && lanes && fl) {
+      // The quantisation grid must be fixed before the first chunk is
+      // projected, yet come from the whole volume: about 1024 rows evenly
+      // spread over it are copied ahead of the chunks (one strided copy into
+      // their places in the device buffer) and sampled; the chunk copies,
+      // which rewrite those rows with the same bytes, wait for the sample.
+      const int64_t rows = M * N;
+      const int64_t rs = rows > 1024 ? rows / 1024 : 1;
+      const size_t row_bytes = (size_t)L * sizeof(float);
+      e = cudaMemcpy2DAsync(const_cast<void*>(volume), rs * row_bytes, host_src, rs * row_bytes,
+                            row_bytes, (size_t)((rows + rs - 1) / rs), cudaMemcpyHostToDevice,
+                            copy_st);
+      if (e == cudaSuccess) e = cudaEventRecord(ev, copy_st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+      if (e != cudaSuccess) return cuda_fail(e, "copy sample rows to device");
+      e = launch_clear_sample(images, 0, nullptr, nullptr, static_cast<const float*>(volume), L, M,
+                              0, N, sample, &ia.nsample, st, rs);
+      if (e != cudaSuccess) return cuda_fail(e, "magnitude sample");
+      ++k1_launches;
+      e = cudaEventRecord(ev, st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(copy_st, ev, 0);
+    }
     for (int64_t z0 = 0; z0 < N && e == cudaSuccess; z0 += zc) {
       const int64_t nz = (N - z0) < zc ? (N - z0) : zc;
       e = cudaMemcpyAsync(static_cast<unsigned char*>(const_cast<void*>(volume)) + z0 * slice,
@@ -327,14 +349,6 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
       if (e == cudaSuccess) e = cudaEventRecord(ev, copy_st);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
       if (e != cudaSuccess) return cuda_fail(e, "copy volume chunk to device");
-      if (lanes && fl && z0 == 0) {
-        // the quantisation grid from the first chunk (2x headroom; a later
-        // voxel beyond it raises the fallback)
-        e = launch_clear_sample(images, 0, nullptr, nullptr, static_cast<const float*>(volume),
-                                L, M, 0, nz, sample, &ia.nsample, st);
-        if (e != cudaSuccess) return cuda_fail(e, "magnitude sample");
-        ++k1_launches;
-      }
       ++k1_launches;
       if (lanes) {
         ia.z0 = z0;

@@ -138,10 +138,12 @@ cudaError_t launch_project_int(const IntProjectArgs& a, cudaStream_t st);
 // Zeroes `bytes` at p (16-byte aligned, a multiple of 16), the status and
 // flags words, and for float volumes (sample != null) writes into
 // sample[0 .. nsample) the maxima of |v| over a sample of rows of slices
-// z0 .. z0 + nz - 1.  Returns the sample length through *nsample.
+// z0 .. z0 + nz - 1: about 4096 rows spread over them, or, with row_stride
+// > 0, exactly the rows 0, row_stride, 2 row_stride, ... (row r = z * M + y
+// counted from slice z0).  Returns the sample length through *nsample.
 cudaError_t launch_clear_sample(void* p, size_t bytes, int* status, int* flags, const float* vol,
                                 int64_t L, int64_t M, int64_t z0, int64_t nz, uint32_t* sample,
-                                int* nsample, cudaStream_t st);
+                                int* nsample, cudaStream_t st, int64_t row_stride = 0);
 constexpr int kMaxSample = 2048;  // sample slots
 
 // Step 2: block partials of every image's 2-D moments into `partials`

@@ -34,7 +34,8 @@ namespace {
 // it saw (float bits; NaN propagates) in sample[b].
 __global__ void clear_sample_kernel(uint4* p, int64_t n16, int* status, int* flags,
                                     const float* vol, int64_t L, int64_t M, int64_t z0,
-                                    int64_t nz, uint32_t* sample, int64_t nsr) {
+                                    int64_t nz, uint32_t* sample, int64_t nsr,
+                                    int64_t row_stride) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if (gid == 0) {
@@ -47,7 +48,8 @@ __global__ void clear_sample_kernel(uint4* p, int64_t n16, int* status, int* fla
   const int64_t step = rows / nsr;  // >= 1
   float m = 0.f;
   for (int64_t j = blockIdx.x; j < nsr; j += gridDim.x) {
-    const int64_t row = j * rows / nsr + (step > 1 ? (j * 7919) % step : 0);
+    const int64_t row =
+        row_stride > 0 ? j * row_stride : j * rows / nsr + (step > 1 ? (j * 7919) % step : 0);
     const int64_t y = row % M, z = z0 + row / M;
     const float* src = vol + (z * M + y) * L;
     for (int64_t x = threadIdx.x; x < L; x += blockDim.x) {
@@ -96,7 +98,7 @@ cudaError_t launch_project_int(const IntProjectArgs& a, cudaStream_t st) {
 
 cudaError_t launch_clear_sample(void* p, size_t bytes, int* status, int* flags, const float* vol,
                                 int64_t L, int64_t M, int64_t z0, int64_t nz, uint32_t* sample,
-                                int* nsample, cudaStream_t st) {
+                                int* nsample, cudaStream_t st, int64_t row_stride) {
   if ((reinterpret_cast<uintptr_t>(p) & 15) != 0 || (bytes & 15) != 0) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -108,9 +110,10 @@ cudaError_t launch_clear_sample(void* p, size_t bytes, int* status, int* flags, 
   if (blocks > cap) blocks = cap;
   int64_t nsr = 0;
   if (sample) {
-    // about 4096 sampled rows (every row of a small volume)
+    // about 4096 sampled rows (every row of a small volume), or every
+    // row_stride-th row
     const int64_t rows = M * nz;
-    nsr = rows < 4096 ? rows : 4096;
+    nsr = row_stride > 0 ? (rows + row_stride - 1) / row_stride : (rows < 4096 ? rows : 4096);
     if (blocks < 64) blocks = 64;
     if (blocks > kMaxSample) blocks = kMaxSample;
     if (blocks > nsr) blocks = nsr;
@@ -118,7 +121,7 @@ cudaError_t launch_clear_sample(void* p, size_t bytes, int* status, int* flags, 
   if (blocks < 1) blocks = 1;
   if (nsample) *nsample = sample ? (int)blocks : 0;
   k1i::clear_sample_kernel<<<(unsigned)blocks, 256, 0, st>>>(
-      static_cast<uint4*>(p), n16, status, flags, vol, L, M, z0, nz, sample, nsr);
+      static_cast<uint4*>(p), n16, status, flags, vol, L, M, z0, nz, sample, nsr, row_stride);
   return cudaGetLastError();
 }
 

@@ -131,7 +131,8 @@ def test_lane_float_voxel_beyond_sampled_grid(dpma):
 @pytest.mark.parametrize("dtype", [np.uint16, np.float32])
 def test_lane_host_path_in_chunks(dpma, dtype):
     """dpma_moments_host copies the volume in even z-chunks and projects each
-    as it lands (the float grid comes from the first chunk)."""
+    as it lands (the float grid comes from rows sampled over the whole volume
+    before the first chunk)."""
     shape = (301, 40, 48)
     if dtype == np.float32:
         vol = synth.mri_like_f32(48, 40, 301, seed=4, n_blobs=5)
@@ -145,6 +146,19 @@ def test_lane_host_path_in_chunks(dpma, dtype):
         assert np.all(np.abs(np.asarray(got) - want) <= TOL * mag)
     else:
         assert dpma.int128_to_ints(got) == oracle.moments(vol, 6)
+
+
+def test_lane_host_path_grid_covers_later_chunks(dpma):
+    """The host path's quantisation grid is sampled from the whole volume, so
+    a volume whose first chunks are faint and whose last ones are 100 times
+    brighter stays on the quantised pipeline and meets the tolerance."""
+    vol = synth.uniform_volume((301, 40, 48), np.float32, 8, low=0.5, high=1.0)
+    vol[200:] *= 100.0
+    got = np.asarray(dpma.moments_host(vol, 6))
+    assert dpma.last_float_path() == 0
+    want = oracle.moments(vol, 6)
+    mag = oracle.moments(vol, 6, absolute=True)
+    assert np.all(np.abs(got - want) <= TOL * mag)
 
 
 def test_lane_async_fallback_gate(dpma):
