@@ -88,6 +88,22 @@ def dist_info():
     return rank, world, local
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks (the slowest replica's time); x itself
+    without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units all replicas processed per second of the slowest one."""
+    return world * units_per_rank / seconds
+
+
 def measured_hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -275,13 +291,9 @@ def run_ours(args):
     dpma.stage_timing(False)
     clk = clocks.stop()
     ms_total = e0.elapsed_time(e1)
-    ms_step = ms_total / args.steps
-    if dist is not None:
-        x = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        ms_step = float(x.item())
+    ms_step = max_over_ranks(ms_total / args.steps, dist, "cuda")
     voxels = float(L * M * N)
-    value = world * voxels / (ms_step * 1e-3)
+    value = whole_job_rate(voxels, world, ms_step * 1e-3)
 
     # roofline of the dominant kernel (fused projection): algorithmic bytes =
     # every voxel read once
@@ -328,12 +340,8 @@ def run_ours(args):
         if rc:
             raise dpma.DpmaError(rc, lib.dpma_last_error().decode())
     barrier()
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    if dist is not None:
-        x = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        e2e_s = float(x.item())
-    e2e = {"value": world * voxels / e2e_s, "unit": UNIT,
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dist, "cuda")
+    e2e = {"value": whole_job_rate(voxels, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(vol.nbytes), "d2h_bytes_per_step": int(out_bytes + 8),
            "ms_per_step": round(e2e_s * 1e3, 4)}
 
@@ -478,8 +486,49 @@ def run_single_rows(dpma, torch, peak):
                  "l2": "256 MB buffer written before every timed call (L2 flush)",
                  "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak,
                               "unit": "GB/s", "frac": round(ach / peak, 4)},
-                 "gpu_launches_per_call": sum(st_n)})
+                 "gpu_launches_per_call": sum(st_n),
+                 "step2_us": step2_routes(dpma, torch, t, 256, 256, 256, dpma.U16, 6, s)})
     return rows
+
+
+def step2_routes(dpma, torch, t, L_, M_, N_, dt, K, s, reps=50):
+    """Device time of step 2 alone on the same projection images (already
+    in L2), by the separable power sums (the pipeline's default) and by the
+    discrete Radon route of Sec. 3.2; both give the same int128 moments."""
+    lib = dpma.lib()
+    P = dpma.num_images(K)
+    npairs = (K + 1) * (K + 2) // 2
+    imgs = torch.empty(dpma.images_size(L_, M_, N_, dt, K) // 4, dtype=torch.int32, device="cuda")
+    m_pow = torch.empty(P * npairs * 4, dtype=torch.int32, device="cuda")
+    m_drt = torch.empty_like(m_pow)
+    ws = torch.empty(dpma.workspace_size(L_, M_, N_, dt, K), dtype=torch.uint8, device="cuda")
+    nd = lib.dpma_drt_workspace_size(L_, M_, N_, dt, K)
+    wd = torch.empty(nd, dtype=torch.uint8, device="cuda")
+    sp = ctypes.c_void_p(s.cuda_stream)
+    ip = ctypes.c_void_p(imgs.data_ptr())
+    lib.dpma_project(ctypes.c_void_p(t.data_ptr()), L_, M_, N_, dt, K, ip, sp)
+
+    def power():
+        lib.dpma_image_moments(ip, L_, M_, N_, dt, K, ctypes.c_void_p(m_pow.data_ptr()), sp,
+                               ctypes.c_void_p(ws.data_ptr()), ws.numel())
+
+    def drt():
+        lib.dpma_image_moments_drt(ip, L_, M_, N_, dt, K, ctypes.c_void_p(m_drt.data_ptr()), sp,
+                                   ctypes.c_void_p(wd.data_ptr()), nd, None)
+    res = {}
+    for name, fn in (("power_sums", power), ("drt", drt)):
+        with torch.cuda.stream(s):
+            for _ in range(5):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                fn()
+            e1.record(s)
+        e1.synchronize()
+        res[name] = round(e0.elapsed_time(e1) * 1e3 / reps, 2)
+    res["identical"] = bool(torch.equal(m_pow, m_drt))
+    return res
 
 
 # ------------------------------------------------ batched and serving rows

@@ -202,6 +202,34 @@ dpma_status dpma_image_moments(const void* images, int64_t L, int64_t M, int64_t
                                void* workspace, size_t workspace_bytes);
 
 /*
+ * Step 2 by the discrete Radon route (Sec. 3.2 and its DRT integral
+ * listing): every image is summed once more onto 1-D integrals along n+1
+ * lattice directions t = alpha f' + beta s' (the paper's five: (1,0), (0,1),
+ * (1,1), (1,-1), (1,2); then (2,1), (1,-2), (2,-1), (1,3), (3,1), (1,-3) for
+ * orders 5..10), their 1-D moments are taken, and the degree-n 2-D moments
+ * follow by an exact rational solve (dpma_drt_plan).  Integer volumes only
+ * (uint32 images as dpma_project writes them); the output `moments2d`
+ * (device, P * (K+1)(K+2)/2 int128) is bit-identical to dpma_image_moments.
+ * `workspace` (device, dpma_drt_workspace_size bytes) may be NULL: the
+ * library then uses its own buffer.  `status` (device int, may be NULL) is
+ * set to 7 if a division of the solve leaves a remainder (images that are
+ * not line sums of any integer volume cannot cause this; a corrupted buffer
+ * can).  Enqueued on `stream`.  DPMA_ERR_INVALID_ARG for float32.
+ */
+dpma_status dpma_image_moments_drt(const void* images, int64_t L, int64_t M, int64_t N,
+                                   dpma_dtype dtype, int K, void* moments2d, void* stream,
+                                   void* workspace, size_t workspace_bytes, int* status);
+/* Bytes of device workspace dpma_image_moments_drt needs (0 for float32 or bad arguments). */
+size_t dpma_drt_workspace_size(int64_t L, int64_t M, int64_t N, dpma_dtype dtype, int K);
+/*
+ * Host only: the directions (alpha[j], beta[j]), j = 0..n, and the exact
+ * solve of degree n of the discrete Radon step:
+ *   T_{n-b,b} = (sum_j E[b*(n+1) + j] * mu_j) / D[b],   mu_j = sum_t t^n P_j(t).
+ * Any pointer may be NULL.  0 <= n <= DPMA_MAX_K.
+ */
+dpma_status dpma_drt_plan(int n, int* alpha, int* beta, int64_t* E, int64_t* D);
+
+/*
  * Step 3 alone (Eqs. 10-16 generalised): 3-D moments from the 2-D moments
  * of dpma_image_moments (device buffers), enqueued on `stream`.  Integer
  * combines are exact (256-bit accumulation, exact division); a division

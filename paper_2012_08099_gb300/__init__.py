@@ -97,6 +97,10 @@ def lib():
                 "dpma_moments_host": (ip, [vp, i64, i64, i64, ip, ip, vp]),
                 "dpma_project": (ip, [vp, i64, i64, i64, ip, ip, vp, vp]),
                 "dpma_image_moments": (ip, [vp, i64, i64, i64, ip, ip, vp, vp, vp, sz]),
+                "dpma_image_moments_drt": (ip, [vp, i64, i64, i64, ip, ip, vp, vp, vp, sz, vp]),
+                "dpma_drt_workspace_size": (sz, [i64, i64, i64, ip, ip]),
+                "dpma_drt_plan": (ip, [ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       P64, P64]),
                 "dpma_combine": (ip, [vp, ip, ip, vp, vp, vp]),
                 "dpma_moments_noalloc": (ip, [vp, i64, i64, i64, ip, ip, vp, vp]),
                 "dpma_stage_timing": (ip, [ip]),
@@ -331,6 +335,47 @@ def image_moments_of(volume, K: int, dtype: int | None = None):
         return f[:, :, 0] + f[:, :, 1]
     vals = int128_to_ints(h.view(np.int64))
     return [vals[k * npairs:(k + 1) * npairs] for k in range(P)]
+
+
+def image_moments_drt_of(volume, K: int, dtype: int | None = None, images=None, status=None):
+    """Steps 1+2 through the C ABI with the discrete Radon step 2
+    (dpma_image_moments_drt): per-image 2-D moments as Python ints.  With
+    ``images`` (a device buffer as dpma_project writes it) step 1 is skipped;
+    ``status`` (an int32 device tensor) receives a remainder flag."""
+    import torch
+    dt = dtype_code(volume) if dtype is None else dtype
+    L, M, N = _shape(volume)
+    P = num_images(K)
+    npairs = (K + 1) * (K + 2) // 2
+    st = _stream_ptr(None)
+    if images is None:
+        images = torch.empty(images_size(L, M, N, dt, K) // 4, dtype=torch.int32,
+                             device=volume.device)
+        _check(lib().dpma_project(ctypes.c_void_p(volume.data_ptr()), L, M, N, dt, K,
+                                  ctypes.c_void_p(images.data_ptr()), st))
+    m2d = torch.empty(P * npairs * 4, dtype=torch.int32, device=volume.device)
+    nws = lib().dpma_drt_workspace_size(L, M, N, dt, K)
+    ws = torch.empty(max(nws, 1), dtype=torch.uint8, device=volume.device)
+    _check(lib().dpma_image_moments_drt(ctypes.c_void_p(images.data_ptr()), L, M, N, dt, K,
+                                        ctypes.c_void_p(m2d.data_ptr()), st,
+                                        ctypes.c_void_p(ws.data_ptr()), nws,
+                                        None if status is None
+                                        else ctypes.c_void_p(status.data_ptr())))
+    torch.cuda.synchronize(volume.device)
+    vals = int128_to_ints(m2d.cpu().numpy().view(np.int64))
+    return [vals[k * npairs:(k + 1) * npairs] for k in range(P)]
+
+
+def drt_plan(n: int):
+    """Host helper: directions [(alpha, beta)] and the exact solve (E rows,
+    D) of degree n of the discrete Radon step 2."""
+    a = (ctypes.c_int * (n + 1))()
+    b = (ctypes.c_int * (n + 1))()
+    E = (ctypes.c_int64 * ((n + 1) * (n + 1)))()
+    D = (ctypes.c_int64 * (n + 1))()
+    _check(lib().dpma_drt_plan(n, a, b, E, D))
+    return ([(a[j], b[j]) for j in range(n + 1)],
+            [[E[r * (n + 1) + j] for j in range(n + 1)] for r in range(n + 1)], list(D))
 
 
 def moments_noalloc(volume, K: int, out, dtype: int | None = None, stream=None):

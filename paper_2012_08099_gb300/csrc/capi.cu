@@ -121,6 +121,8 @@ struct DeviceState {
   cudaStream_t copy_stream = nullptr;  // host-to-device chunks of dpma_moments_host
   cudaEvent_t chunk_ready = nullptr;
   int* h_status = nullptr;  // pinned: the synchronous calls read the status word here
+  void* drt_ws = nullptr;   // workspace of dpma_image_moments_drt without a caller workspace
+  size_t drt_ws_bytes = 0;
 };
 
 // The pinned host word that receives the device status (a pageable
@@ -633,6 +635,49 @@ dpma_status dpma_image_moments(const void* images, int64_t L, int64_t M, int64_t
   part = static_cast<unsigned char*>(ds->ws) + w.off_part;
   e = launch_image_moments(images, w.set, K, is_float(dtype), part, moments2d, st);
   if (e != cudaSuccess) return cuda_fail(e, "image moment kernel");
+  return DPMA_OK;
+}
+
+size_t dpma_drt_workspace_size(int64_t L, int64_t M, int64_t N, dpma_dtype dtype, int K) {
+  if (check_args(L, M, N, dtype, K) != DPMA_OK || is_float(dtype)) return 0;
+  return drt_workspace_bytes(L, M, N, K);
+}
+
+dpma_status dpma_image_moments_drt(const void* images, int64_t L, int64_t M, int64_t N,
+                                   dpma_dtype dtype, int K, void* moments2d, void* stream,
+                                   void* workspace, size_t workspace_bytes, int* status) {
+  if (!images || !moments2d) return fail(DPMA_ERR_INVALID_ARG, "null image or output pointer");
+  if (is_float(dtype))
+    return fail(DPMA_ERR_INVALID_ARG, "the discrete Radon step takes integer images only");
+  dpma_status s = check_args(L, M, N, dtype, K);
+  if (s != DPMA_OK) return s;
+  const size_t need = drt_workspace_bytes(L, M, N, K);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (workspace) {
+    if (workspace_bytes < need) return fail(DPMA_ERR_INVALID_ARG, "workspace too small");
+    cudaError_t e = launch_image_moments_drt(images, L, M, N, K, workspace, moments2d, status, st);
+    if (e != cudaSuccess) return cuda_fail(e, "discrete Radon moment kernels");
+    return DPMA_OK;
+  }
+  DeviceState* ds = state_for_current_device(nullptr);
+  if (!ds) return fail(DPMA_ERR_CUDA, "no current CUDA device");
+  std::lock_guard<std::mutex> lk(ds->mu);
+  cudaError_t e = ensure_buffer(&ds->drt_ws, &ds->drt_ws_bytes, need);
+  if (e != cudaSuccess) return cuda_fail(e, "discrete Radon workspace");
+  e = launch_image_moments_drt(images, L, M, N, K, ds->drt_ws, moments2d, status, st);
+  if (e != cudaSuccess) return cuda_fail(e, "discrete Radon moment kernels");
+  return DPMA_OK;
+}
+
+dpma_status dpma_drt_plan(int n, int* alpha, int* beta, int64_t* E, int64_t* D) {
+  if (n < 0 || n > DPMA_MAX_K) return fail(DPMA_ERR_INVALID_ARG, "degree out of range");
+  for (int j = 0; j <= n; ++j) {
+    int a = 0, b = 0;
+    drt_direction(j, &a, &b);
+    if (alpha) alpha[j] = a;
+    if (beta) beta[j] = b;
+  }
+  if (!drt_plan_degree(n, E, D)) return fail(DPMA_ERR_INTERNAL, "discrete Radon solve unavailable");
   return DPMA_OK;
 }
 

@@ -146,6 +146,15 @@ cudaError_t launch_clear_sample(void* p, size_t bytes, int* status, int* flags, 
                                 int* nsample, cudaStream_t st, int64_t row_stride = 0);
 constexpr int kMaxSample = 2048;  // sample slots
 
+// Step 2 by the discrete Radon route (k2_drt.cu): integer images only.
+size_t drt_workspace_bytes(int64_t L, int64_t M, int64_t N, int K);
+cudaError_t launch_image_moments_drt(const void* images, int64_t L, int64_t M, int64_t N, int K,
+                                     void* workspace, void* m2d, int* status, cudaStream_t st);
+// Host: direction j of the 1-D integrals, and the exact solve of degree n
+// (E row-major [b][j], (n+1) x (n+1); D[b]); false if unavailable.
+int drt_direction(int j, int* alpha, int* beta);
+bool drt_plan_degree(int n, int64_t* E, int64_t* D);
+
 // Step 2: block partials of every image's 2-D moments into `partials`
 // (int128 or float pairs), then a reduction into `m2d`.
 size_t moments2d_partials_bytes(const ImageSet& set, int K, bool is_float);

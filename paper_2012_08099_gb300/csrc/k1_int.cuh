@@ -342,10 +342,12 @@ __device__ __forceinline__ int block_pos(int br, int bc) {
 }
 
 // The micro-tile of a group-A lane, both slices: NR rows of NC voxels
-// starting at (row y, column x) of the stage, as NL limbs each (`ok` false:
-// zeros).
+// starting at (row y, column x) of the stage, as NL limbs each.  After a wait
+// that gave up the stage holds undefined values; they feed only the sums of
+// that step, after which every thread leaves and the call reports the
+// timeout, so they are not masked.
 template <typename T, int NR, int NC, int NL, int TXc, int TYc>
-__device__ __forceinline__ void load_tile(const T* sb, int y, int x, bool ok, float s1, float g1,
+__device__ __forceinline__ void load_tile(const T* sb, int y, int x, float s1, float g1,
                                           float s2, float& vmax, uint32_t (&v)[2][NR][NC][NL]) {
   constexpr bool FL = std::is_same<T, float>::value;
   using V = typename std::conditional<FL, float, uint32_t>::type;
@@ -358,9 +360,9 @@ __device__ __forceinline__ void load_tile(const T* sb, int y, int x, bool ok, fl
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         if constexpr (FL) {
-          quantise(ok ? raw[c] : 0.f, s1, g1, s2, v[sl][r][c][0], v[sl][r][c][NL - 1], vmax);
+          quantise(raw[c], s1, g1, s2, v[sl][r][c][0], v[sl][r][c][NL - 1], vmax);
         } else {
-          v[sl][r][c][0] = ok ? raw[c] : 0u;
+          v[sl][r][c][0] = raw[c];
         }
       }
     }
@@ -585,8 +587,8 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
                                           p.wait_budget);
         if (!ok) *abort_flag = 1;
         uint32_t v[2][BYA][RA][NL];
-        load_tile<T, BYA, RA, NL, TXc, TYc>(stage + (size_t)st * 2 * TYc * TXc, yl, xl, ok, s1,
-                                            g1, s2, vmax, v);
+        load_tile<T, BYA, RA, NL, TXc, TYc>(stage + (size_t)st * 2 * TYc * TXc, yl, xl, s1, g1,
+                                            s2, vmax, v);
         // the micro-tile for group B, as blocks of 2 rows x BB columns
 #pragma unroll
         for (int sl = 0; sl < 2; ++sl)
