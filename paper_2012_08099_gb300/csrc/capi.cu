@@ -168,6 +168,7 @@ struct StageEvent {
   int stage;
   int kernels;  // kernel launches the stage made
   cudaEvent_t a, b;
+  bool free_a;  // a is the call's first event (b of a stage is a of the next)
 };
 std::mutex g_timing_mu;
 bool g_timing = false;
@@ -187,8 +188,10 @@ cudaEvent_t take_event() {
   return e;
 }
 
+// One event per stage boundary: the event that ends a stage starts the next.
 struct StageRecorder {
   bool on;
+  bool first = true;
   cudaStream_t st;
   cudaEvent_t last = nullptr;
   explicit StageRecorder(cudaStream_t s) : st(s) {
@@ -201,14 +204,14 @@ struct StageRecorder {
     std::lock_guard<std::mutex> lk(g_timing_mu);
     cudaEvent_t e = take_event();
     cudaEventRecord(e, st);
-    g_pending.push_back({stage, kernels, last, e});
-    last = take_event();
-    cudaEventRecord(last, st);
+    g_pending.push_back({stage, kernels, last, e, first});
+    first = false;
+    last = e;
   }
   ~StageRecorder() {
-    if (!on) return;
+    if (!on || !first) return;
     std::lock_guard<std::mutex> lk(g_timing_mu);
-    g_free_events.push_back(last);
+    g_free_events.push_back(last);  // recorded but never used
   }
 };
 
@@ -251,6 +254,149 @@ dpma_status enqueue_float_fallback(const void* volume, int64_t L, int64_t M, int
   e = launch_combine(ws + w.off_m2d, K, true, out, status, st, gate);
   if (e != cudaSuccess) return cuda_fail(e, "combine kernel (fallback)");
   return DPMA_OK;
+}
+
+// The fallback as one graph launch.  Five gated launches cost about 25 us of
+// stream time even when the gate is closed, so a pipeline that repeats with
+// the same buffers runs them as a cached executable graph instead: a
+// one-thread gate kernel reads the flags word and sets the condition of an
+// IF node whose body is the five launches (captured from
+// enqueue_float_fallback; the body's kernels keep their own gate test).  The
+// graph bakes in every pointer and size, so it is keyed by all of them, and
+// a key is promoted to a graph only when it is seen a second time: one-off
+// calls keep the plain gated launches and pay no graph construction.
+__global__ void fallback_gate_kernel(const int* flags, cudaGraphConditionalHandle h) {
+  cudaGraphSetConditional(h, (*flags & 3) ? 1u : 0u);
+}
+
+struct FallbackKey {
+  int dev;
+  const void* vol;
+  int64_t L, M, N;
+  int K;
+  void* out;
+  unsigned char* ws;
+  bool operator==(const FallbackKey& o) const {
+    return dev == o.dev && vol == o.vol && L == o.L && M == o.M && N == o.N && K == o.K &&
+           out == o.out && ws == o.ws;
+  }
+};
+struct FallbackGraph {
+  FallbackKey key;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+constexpr size_t kFallbackGraphs = 8;   // cached executable graphs (least recently used out)
+constexpr size_t kFallbackSeen = 16;    // keys seen once
+std::mutex g_fb_mu;
+std::vector<FallbackGraph> g_fb_graphs;  // most recently used last
+std::vector<FallbackKey> g_fb_seen;
+
+cudaError_t build_fallback_graph(const FallbackKey& k, cudaStream_t cap, const Layout& w,
+                                 FallbackGraph* out) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  auto fail = [&](cudaError_t err) {
+    cudaGraphDestroy(g);
+    return err;
+  };
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+  if (e != cudaSuccess) return fail(e);
+  const int* flags = reinterpret_cast<const int*>(k.ws + w.off_status) + 1;
+  void* args[] = {&flags, &h};
+  cudaKernelNodeParams kp{};
+  kp.func = reinterpret_cast<void*>(fallback_gate_kernel);
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(1);
+  kp.kernelParams = args;
+  cudaGraphNode_t gate;
+  e = cudaGraphAddKernelNode(&gate, g, nullptr, 0, &kp);
+  if (e != cudaSuccess) return fail(e);
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeIf;
+  np.conditional.size = 1;
+  cudaGraphNode_t cond;
+  e = cudaGraphAddNode(&cond, g, &gate, nullptr, 1, &np);
+  if (e != cudaSuccess) return fail(e);
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return fail(e);
+  const dpma_status fs = enqueue_float_fallback(k.vol, k.L, k.M, k.N, k.K, k.out, cap, k.ws, w);
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(cap, &captured);
+  if (fs != DPMA_OK) return fail(cudaErrorUnknown);
+  if (e != cudaSuccess) return fail(e);
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, g, 0);
+  if (e != cudaSuccess) return fail(e);
+  out->key = k;
+  out->graph = g;
+  out->exec = exec;
+  return cudaSuccess;
+}
+
+// Enqueues the fallback on st: the cached graph of this key, else (building
+// it on a key's second use) the plain gated launches.  *launches receives the
+// kernel launches issued from the host.
+dpma_status enqueue_fallback(const void* volume, int64_t L, int64_t M, int64_t N, int K,
+                             void* out, cudaStream_t st, unsigned char* ws, const Layout& w,
+                             int* launches) {
+  FallbackKey k{};
+  if (cudaGetDevice(&k.dev) != cudaSuccess) k.dev = -1;
+  k.vol = volume; k.L = L; k.M = M; k.N = N; k.K = K; k.out = out; k.ws = ws;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const bool capturing = cudaStreamIsCapturing(st, &cs) == cudaSuccess &&
+                         cs != cudaStreamCaptureStatusNone;
+  if (k.dev >= 0 && !capturing) {
+    std::lock_guard<std::mutex> lk(g_fb_mu);
+    cudaGraphExec_t exec = nullptr;
+    for (size_t i = 0; i < g_fb_graphs.size(); ++i)
+      if (g_fb_graphs[i].key == k) {
+        FallbackGraph fg = g_fb_graphs[i];
+        g_fb_graphs.erase(g_fb_graphs.begin() + i);
+        g_fb_graphs.push_back(fg);
+        exec = fg.exec;
+        break;
+      }
+    if (!exec) {
+      bool seen = false;
+      for (const FallbackKey& o : g_fb_seen) seen = seen || (o == k);
+      if (seen) {
+        cudaStream_t cap = nullptr;
+        FallbackGraph fg;
+        cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = build_fallback_graph(k, cap, w, &fg);
+        if (cap) cudaStreamDestroy(cap);
+        if (e == cudaSuccess) {
+          if (g_fb_graphs.size() >= kFallbackGraphs) {
+            cudaGraphExecDestroy(g_fb_graphs.front().exec);
+            cudaGraphDestroy(g_fb_graphs.front().graph);
+            g_fb_graphs.erase(g_fb_graphs.begin());
+          }
+          g_fb_graphs.push_back(fg);
+          exec = fg.exec;
+        } else {
+          cudaGetLastError();  // a failed build leaves the plain launches in use
+        }
+      } else {
+        if (g_fb_seen.size() >= kFallbackSeen) g_fb_seen.erase(g_fb_seen.begin());
+        g_fb_seen.push_back(k);
+      }
+    }
+    if (exec) {
+      const cudaError_t e = cudaGraphLaunch(exec, st);
+      if (e != cudaSuccess) return cuda_fail(e, "fallback graph launch");
+      *launches = 1;
+      return DPMA_OK;
+    }
+  }
+  *launches = 5;
+  return enqueue_float_fallback(volume, L, M, N, K, out, st, ws, w);
 }
 
 // The pipeline on stream st.  With a host source (host_src non-null) the
@@ -382,10 +528,12 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
     e = launch_combine_fixed(ws + w.off_m2d, K, w.set.P, static_cast<double*>(out), status, flags,
                              scale, L, M, N, kFloatTolerance, st);
     if (e != cudaSuccess) return cuda_fail(e, "combine kernel");
-    // the combine and the five gated fallback launches (clear, projection,
-    // image moments + reduction, combine) count as the last stage
-    const dpma_status fs = enqueue_float_fallback(volume, L, M, N, K, out, st, ws, w);
-    rec.mark(3, 6);
+    // the combine and the gated fallback (five launches, or one graph
+    // launch of a one-thread gate and a conditional body) count as the last
+    // stage
+    int fb_launches = 0;
+    const dpma_status fs = enqueue_fallback(volume, L, M, N, K, out, st, ws, w, &fb_launches);
+    rec.mark(3, 1 + fb_launches);
     return fs;
   }
   e = launch_image_moments(images, w.set, K, fl, ws + w.off_part, ws + w.off_m2d, st);
@@ -746,7 +894,7 @@ dpma_status dpma_stage_times(double* ms, int64_t* launches, int reset) {
     }
     g_stage_ms[se.stage] += t;
     g_stage_launches[se.stage] += se.kernels;
-    g_free_events.push_back(se.a);
+    if (se.free_a) g_free_events.push_back(se.a);
     g_free_events.push_back(se.b);
   }
   g_pending.clear();

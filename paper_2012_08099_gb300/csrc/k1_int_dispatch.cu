@@ -47,12 +47,17 @@ __global__ void clear_sample_kernel(uint4* p, int64_t n16, int* status, int* fla
   const int64_t rows = M * nz;
   const int64_t step = rows / nsr;  // >= 1
   float m = 0.f;
-  for (int64_t j = blockIdx.x; j < nsr; j += gridDim.x) {
+  // one sampled row per warp at a time, so every warp's loads are in flight
+  // together (one memory round trip per row instead of one per block row)
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int lane = threadIdx.x & 31;
+  for (int64_t j = gid >> 5; j < nsr; j += warps) {
     const int64_t row =
         row_stride > 0 ? j * row_stride : j * rows / nsr + (step > 1 ? (j * 7919) % step : 0);
     const int64_t y = row % M, z = z0 + row / M;
     const float* src = vol + (z * M + y) * L;
-    for (int64_t x = threadIdx.x; x < L; x += blockDim.x) {
+#pragma unroll 4
+    for (int64_t x = lane; x < L; x += 32) {
       float d;
       asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(m), "f"(fabsf(__ldcs(src + x))));
       m = d;

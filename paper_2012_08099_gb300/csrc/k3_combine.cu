@@ -118,23 +118,21 @@ __device__ __forceinline__ void mac256(I256& a, int64_t c, i128 t) {
   add256(a, prod);
 }
 
-// q = a / d exactly; returns false on a remainder or if q leaves int128.
-__device__ bool div256_exact(I256 a, int64_t d, i128* q) {
-  const bool neg = (a.w[3] >> 63) != 0;
-  if (neg) neg256(a);
-  uint64_t qw[4];
-  u128 rem = 0;
-  for (int i = 3; i >= 0; --i) {
-    const u128 cur = (rem << 64) | a.w[i];
-    qw[i] = (uint64_t)(cur / (uint64_t)d);
-    rem = cur % (uint64_t)d;
-  }
-  if (rem != 0) return false;
-  if (qw[3] != 0 || qw[2] != 0) return false;
-  const u128 mag = ((u128)qw[1] << 64) | qw[0];
-  if (!neg && (mag >> 127)) return false;
-  if (neg && mag > ((u128)1 << 127)) return false;
-  *q = neg ? (i128)(~mag + 1) : (i128)mag;
+// q = a / d exactly for d = odd << sh, with inv the inverse of odd modulo
+// 2^128: when the division is exact the quotient is the low 128 bits of
+// (a >> sh) * inv, and multiplying back reproduces a in 256 bits; a
+// remainder or a quotient outside int128 fails that check.  Two 128-bit
+// products instead of four long divisions.
+__device__ bool div_exact_inv(const I256& a, int64_t d, int sh, u128 inv, i128* q) {
+  const u128 lo = ((u128)a.w[1] << 64) | a.w[0];
+  const u128 hi = ((u128)a.w[3] << 64) | a.w[2];
+  const u128 as = sh ? ((lo >> sh) | (hi << (128 - sh))) : lo;
+  const i128 qc = (i128)(as * inv);
+  I256 back = {{0, 0, 0, 0}};
+  mac256(back, d, qc);
+  if (back.w[0] != a.w[0] || back.w[1] != a.w[1] || back.w[2] != a.w[2] || back.w[3] != a.w[3])
+    return false;
+  *q = qc;
   return true;
 }
 
@@ -145,6 +143,8 @@ __device__ bool div256_exact(I256 a, int64_t d, i128* q) {
 struct CombParams {
   const int64_t* plan;
   int off[kMaxK + 1];
+  int dshift[kMaxK + 1];       // D_n = odd << dshift[n]
+  uint64_t dinv[kMaxK + 1][2];  // odd^-1 mod 2^128 (low, high)
   int K, npairs;
   const void* m2d;
   void* out;
@@ -192,7 +192,8 @@ __global__ void combine_int_kernel(CombParams p) {
   }
   if (lane != 0) return;
   i128 q = 0;
-  if (!div256_exact(acc, D, &q)) {
+  const u128 inv = ((u128)p.dinv[n][1] << 64) | p.dinv[n][0];
+  if (!div_exact_inv(acc, D, p.dshift[n], inv, &q)) {
     if (p.status) atomicCAS(p.status, 0, kStatusInternal);  // a timeout (5) stays
     q = 0;
   }
@@ -237,6 +238,8 @@ __global__ void combine_f32_kernel(CombParams p) {
 struct FixedParams {
   const int64_t* plan;
   int off[kMaxK + 1];
+  int dshift[kMaxK + 1];
+  uint64_t dinv[kMaxK + 1][2];
   int K, npairs, P;
   const void* m2d;
   double* out;
@@ -306,7 +309,9 @@ __global__ void combine_fixed_kernel(FixedParams p) {
   i128 q0 = 0, q1 = 0;
   // a remainder (impossible for images of a volume) also sends the volume
   // to the fallback, which recomputes it
-  const bool ok = div256_exact(acc0, D, &q0) && div256_exact(acc1, D, &q1);
+  const u128 inv = ((u128)p.dinv[n][1] << 64) | p.dinv[n][0];
+  const bool ok = div_exact_inv(acc0, D, p.dshift[n], inv, &q0) &&
+                  div_exact_inv(acc1, D, p.dshift[n], inv, &q1);
   // Q = q0 * 2^(B+1) + q1, exactly, in 256 bits
   I256 q;
   {
@@ -337,9 +342,30 @@ __global__ void combine_fixed_kernel(FixedParams p) {
   if (!ok || !(bound <= p.tol * (fabs(val) - bound))) atomicOr(p.flags, 2);
 }
 
+// For every degree of plan cp: D_n = odd << dshift[n] and odd^-1 modulo
+// 2^128 (Newton's iteration x <- x (2 - odd x), which doubles the correct
+// low bits from 3 at x = odd).  Host only.
+bool divisor_inverses(const CombinePlan& cp, int dshift[kMaxK + 1], uint64_t dinv[kMaxK + 1][2]) {
+  for (int n = 0; n <= kMaxK; ++n) { dshift[n] = 0; dinv[n][0] = dinv[n][1] = 0; }
+  for (int n = 0; n <= cp.K; ++n) {
+    uint64_t odd = (uint64_t)cp.deg[n].D;
+    int sh = 0;
+    while (odd && (odd & 1) == 0) { odd >>= 1; ++sh; }
+    if (odd == 0) return false;
+    u128 x = odd;
+    for (int it = 0; it < 7; ++it) x *= (u128)2 - (u128)odd * x;
+    dshift[n] = sh;
+    dinv[n][0] = (uint64_t)x;
+    dinv[n][1] = (uint64_t)(x >> 64);
+  }
+  return true;
+}
+
 struct DevPlan {
   int64_t* words;
   int off[kMaxK + 1];
+  int dshift[kMaxK + 1];
+  uint64_t dinv[kMaxK + 1][2];
 };
 
 std::mutex g_mu;
@@ -357,6 +383,7 @@ cudaError_t device_plan(int K, DevPlan* out) {
   if (!cp) return cudaErrorInvalidValue;
   std::vector<int64_t> w;
   DevPlan dp{};
+  if (!divisor_inverses(*cp, dp.dshift, dp.dinv)) return cudaErrorInvalidValue;
   for (int n = 0; n <= K; ++n) {
     const DegreePlan& d = cp->deg[n];
     dp.off[n] = (int)w.size();
@@ -438,7 +465,12 @@ cudaError_t launch_combine(const void* m2d, int K, bool is_float, void* out, int
   CombParams p{};
   p.gate = gate;
   p.plan = dp.words;
-  for (int n = 0; n <= kMaxK; ++n) p.off[n] = dp.off[n];
+  for (int n = 0; n <= kMaxK; ++n) {
+    p.off[n] = dp.off[n];
+    p.dshift[n] = dp.dshift[n];
+    p.dinv[n][0] = dp.dinv[n][0];
+    p.dinv[n][1] = dp.dinv[n][1];
+  }
   p.K = K;
   p.npairs = num_2d(K);
   p.m2d = m2d;
@@ -460,7 +492,12 @@ cudaError_t launch_combine_fixed(const void* m2d, int K, int P, double* out, int
   if (e != cudaSuccess) return e;
   FixedParams p{};
   p.plan = dp.words;
-  for (int n = 0; n <= kMaxK; ++n) p.off[n] = dp.off[n];
+  for (int n = 0; n <= kMaxK; ++n) {
+    p.off[n] = dp.off[n];
+    p.dshift[n] = dp.dshift[n];
+    p.dinv[n][0] = dp.dinv[n][0];
+    p.dinv[n][1] = dp.dinv[n][1];
+  }
   p.K = K;
   p.npairs = num_2d(K);
   p.P = P;
@@ -507,6 +544,8 @@ cudaError_t launch_combine_packed(const int64_t* dev_words, const int off[kMaxK 
   CombParams p{};
   p.plan = dev_words;
   for (int n = 0; n <= kMaxK; ++n) p.off[n] = off[n];
+  const CombinePlan* cp = combine_plan(K);
+  if (!cp || !divisor_inverses(*cp, p.dshift, p.dinv)) return cudaErrorInvalidValue;
   p.K = K;
   p.npairs = num_2d(K);
   p.m2d = m2d;

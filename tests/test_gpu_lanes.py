@@ -177,6 +177,33 @@ def test_lane_async_fallback_gate(dpma):
     assert np.all(np.abs(got - want) <= TOL * mag)
 
 
+def test_lane_fallback_graph_repeated_calls(dpma):
+    """Repeated dpma_moments_async calls with the same buffers run the
+    fallback as a cached graph (gate kernel + conditional body) from the
+    second call on.  The buffer's contents alternate between a volume the
+    quantised pipeline serves and one that needs the fallback: every result
+    must meet the tolerance, so the condition is taken exactly when needed."""
+    shape = (12, 30, 32)
+    good = synth.uniform_volume(shape, np.float32, 31, low=0.5, high=1.0)
+    bad = good.copy()
+    bad[3, 4, 5] = 2.0 ** 40
+    t = torch.empty(shape, dtype=torch.float32, device="cuda")
+    nm = dpma.num_moments(4)
+    out = torch.empty(nm, dtype=torch.float64, device="cuda")
+    ws = torch.empty(dpma.workspace_size(32, 30, 12, dpma.F32, 4), dtype=torch.uint8,
+                     device="cuda")
+    want = {}
+    for name, v in (("good", good), ("bad", bad)):
+        want[name] = (oracle.moments(v, 4), oracle.moments(v, 4, absolute=True))
+    for i, name in enumerate(["good", "good", "bad", "good", "bad", "bad", "good"]):
+        t.copy_(torch.from_numpy(good if name == "good" else bad))
+        dpma.moments_async(t, 4, out, dpma.F32, workspace=ws)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        w, mag = want[name]
+        assert np.all(np.abs(got - w) <= TOL * mag), (i, name)
+
+
 @pytest.mark.parametrize("dtype", [np.uint16, np.float32])
 def test_bounded_wait_runs_out(dpma, dtype):
     """With a one-cycle wait budget the first pending copy of every CTA is not
