@@ -943,14 +943,25 @@ cudaError_t prepare_plans() {
 
 cudaError_t enqueue_fused(const BTask* d_tasks, const int* d_order, int n, int max_K,
                           int* d_counters, i128* d_T, const FusedGroup* groups, int ngroups,
-                          void* out, int* d_status, cudaStream_t st) {
+                          void* out, int* d_status, cudaStream_t st, const Fork* fk) {
   if (n <= 0) return cudaSuccess;
   const DevPlans* dp = nullptr;
   cudaError_t e = plans_for_device(&dp);
   if (e != cudaSuccess) return e;
+  // Two groups run concurrently when a fork is given: the second group's
+  // CTAs take each SM as soon as the first group's CTA there has drained its
+  // queue, so the first launch's tail overlaps the second launch.
+  const bool concurrent = fk && fk->side && ngroups == 2 && groups[0].count > 0 &&
+                          groups[1].count > 0;
+  if (concurrent) {
+    e = cudaEventRecord(fk->fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(fk->side, fk->fork, 0);
+    if (e != cudaSuccess) return e;
+  }
   for (int g = 0; g < ngroups; ++g) {
     const FusedGroup& G = groups[g];
     if (G.count <= 0) continue;
+    const cudaStream_t gs = (concurrent && g == 1) ? fk->side : st;
     FusedParams p{};
     p.tasks = d_tasks;
     p.order = d_order + G.first;
@@ -961,13 +972,18 @@ cudaError_t enqueue_fused(const BTask* d_tasks, const int* d_order, int n, int m
     if (G.threads == 512) {
       e = set_smem<512>(G.smem);
       if (e != cudaSuccess) return e;
-      batch_fused_kernel<512><<<G.grid, 512, G.smem, st>>>(p);
+      batch_fused_kernel<512><<<G.grid, 512, G.smem, gs>>>(p);
     } else {
       e = set_smem<256>(G.smem);
       if (e != cudaSuccess) return e;
-      batch_fused_kernel<256><<<G.grid, 256, G.smem, st>>>(p);
+      batch_fused_kernel<256><<<G.grid, 256, G.smem, gs>>>(p);
     }
     e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (concurrent) {
+    e = cudaEventRecord(fk->join, fk->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, fk->join, 0);
     if (e != cudaSuccess) return e;
   }
   BCombParams cp{};
@@ -1010,6 +1026,7 @@ struct dpma_batch {
   int sms = 1;
   void* d_ws = nullptr;  // workspace of the single-volume path
   size_t ws_bytes = 0;
+  batch::Fork fork;      // side stream and events of the concurrent second launch
 };
 
 namespace {
@@ -1022,6 +1039,9 @@ void free_plan(dpma_batch* b) {
   cudaFree(b->d_status);
   cudaFree(b->d_T);
   cudaFree(b->d_ws);
+  if (b->fork.side) cudaStreamDestroy(b->fork.side);
+  if (b->fork.fork) cudaEventDestroy(b->fork.fork);
+  if (b->fork.join) cudaEventDestroy(b->fork.join);
   delete b;
 }
 
@@ -1071,9 +1091,14 @@ dpma_status enqueue_batch(dpma_batch* b, void* out, cudaStream_t st, bool single
   const int n = (int)b->cls.tasks.size();
   if (n > 0) {
     e = cudaMemsetAsync(b->d_counter, 0, sizeof(int) * batch::kMaxGroups, st);
+    if (e == cudaSuccess && b->ngroups == 2 && !b->fork.side) {
+      e = cudaStreamCreateWithFlags(&b->fork.side, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork.fork, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork.join, cudaEventDisableTiming);
+    }
     if (e == cudaSuccess)
       e = batch::enqueue_fused(b->d_tasks, b->d_order, n, b->cls.max_K, b->d_counter, b->d_T,
-                               b->groups, b->ngroups, out, b->d_status, st);
+                               b->groups, b->ngroups, out, b->d_status, st, &b->fork);
     if (e != cudaSuccess)
       return bfail(DPMA_ERR_CUDA, std::string("batched kernels: ") + cudaGetErrorString(e));
   }

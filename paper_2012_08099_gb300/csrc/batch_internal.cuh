@@ -65,15 +65,21 @@ struct FusedGroup {
 };
 constexpr int kMaxGroups = 2;
 
-// Enqueues the fused projection + 2-D moment launches of the groups (one
-// after another, each with its own queue counter d_counters[g], which must
-// be zero when the launch starts: the caller clears them) and the batched
-// combine for all n tasks already in device memory, whose highest order is
-// max_K; `out` is the base the tasks' out_off refer to; *d_status becomes 7
-// if an exact division left a remainder.
+// Enqueues the fused projection + 2-D moment launches of the groups (each
+// with its own queue counter d_counters[g], which must be zero when the
+// launch starts: the caller clears them) and the batched combine for all n
+// tasks already in device memory, whose highest order is max_K; `out` is the
+// base the tasks' out_off refer to; *d_status becomes 7 if an exact division
+// left a remainder.  With a side stream and two events (fork, join) the
+// second group runs on `side`, concurrently with the first, and the combine
+// waits for both; otherwise the groups run one after another on st.
+struct Fork {
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
 cudaError_t enqueue_fused(const BTask* d_tasks, const int* d_order, int n, int max_K,
                           int* d_counters, i128* d_T, const FusedGroup* groups, int ngroups,
-                          void* out, int* d_status, cudaStream_t st);
+                          void* out, int* d_status, cudaStream_t st, const Fork* fk = nullptr);
 // Enqueues *dst = max(*dst, *src) on the device.
 cudaError_t enqueue_merge_status(const int* src, int* dst, cudaStream_t st);
 

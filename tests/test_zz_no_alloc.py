@@ -7,7 +7,8 @@ dpma_moments_noalloc keeps its workspace in a static device array.  Called
 through the C ABI twice in a row, it must reproduce dpma_moments: exactly
 for integer volumes, within the float tolerance of the other GPU tests
 (1e-6 of the moment of |V|) for float32 volumes.  This file is collected
-last so a failure here leaves every other test already run.
+last so a failure here leaves every other test already run.  The results
+are also compared with the oracle (Eq. 2).
 """
 import ctypes
 
@@ -61,8 +62,11 @@ def test_noalloc_matches_dpma_moments_twice(dpma, dtype, shape, K):
         if dt == dpma.F32:
             mag = oracle.moments(vol, K, absolute=True)
             assert np.all(np.abs(got - ref) <= 1e-6 * mag)
+            assert np.all(np.abs(got - oracle.moments(vol, K)) <= 1e-6 * mag)
         else:
             np.testing.assert_array_equal(got, ref)
+            # and the definition itself (Eq. 2), bit for bit
+            assert dpma.int128_to_ints(got) == oracle.moments(vol, K)
 
 
 def test_noalloc_refuses_volumes_beyond_its_scratch(dpma):
