@@ -204,6 +204,35 @@ def test_lane_fallback_graph_repeated_calls(dpma):
         assert np.all(np.abs(got - w) <= TOL * mag), (i, name)
 
 
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16, np.float32])
+def test_repeated_calls_replay_one_graph(dpma, dtype):
+    """From its second call with the same buffers a device-resident pipeline
+    is replayed as one cached graph (stage timing off).  The buffer's
+    contents change between calls; every result must match the oracle
+    (integers bit for bit, float32 within the tolerance)."""
+    shape = (21, 37, 48)
+    N, M, L = shape
+    K = 6
+    torch_dt = {np.uint8: torch.uint8, np.uint16: torch.int16, np.float32: torch.float32}[dtype]
+    t = torch.empty(shape, dtype=torch_dt, device="cuda")
+    dt = {np.uint8: dpma.U8, np.uint16: dpma.U16, np.float32: dpma.F32}[dtype]
+    nm = dpma.num_moments(K)
+    out = torch.empty(nm * (1 if dtype == np.float32 else 2),
+                      dtype=torch.float64 if dtype == np.float32 else torch.int64, device="cuda")
+    ws = torch.empty(dpma.workspace_size(L, M, N, dt, K), dtype=torch.uint8, device="cuda")
+    for i in range(5):
+        vol = synth.uniform_volume(shape, dtype, seed=100 + i)
+        t.copy_(torch.from_numpy(vol.view(np.int16) if dtype == np.uint16 else vol))
+        dpma.moments_async(t, K, out, dt, workspace=ws)
+        torch.cuda.synchronize()
+        want = oracle.moments(vol, K)
+        if dtype == np.float32:
+            mag = oracle.moments(vol, K, absolute=True)
+            assert np.all(np.abs(out.cpu().numpy() - want) <= TOL * mag), i
+        else:
+            assert dpma.int128_to_ints(out.cpu().numpy()) == want, i
+
+
 @pytest.mark.parametrize("dtype", [np.uint16, np.float32])
 def test_bounded_wait_runs_out(dpma, dtype):
     """With a one-cycle wait budget the first pending copy of every CTA is not
