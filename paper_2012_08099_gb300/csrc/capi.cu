@@ -497,7 +497,7 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
       if (e == cudaSuccess) e = cudaEventRecord(ev, copy_st);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
       if (e != cudaSuccess) return cuda_fail(e, "copy volume chunk to device");
-      ++k1_launches;
+      k1_launches += w.set.P > 9 ? 2 : 1;  // images 9, 10 in a second kernel
       if (lanes) {
         ia.z0 = z0;
         ia.nz = nz;
@@ -517,7 +517,7 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
       e = launch_project(a, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "projection kernel");
-    k1_launches = 1;
+    k1_launches = w.set.P > 9 ? 2 : 1;
   }
   rec.mark(1, k1_launches);
   if (lanes && fl) {

@@ -91,8 +91,11 @@ template <typename T, int P> struct Cfg {
   static constexpr int STAGE = 2 * SLICE;  // one z-pair
   // ring depth: about 96 KB of z-pairs in flight
   static constexpr int STAGES = (98304 / STAGE) < 2 ? 2 : (98304 / STAGE > 16 ? 16 : 98304 / STAGE);
-  static constexpr bool H3 = P > 3, H4 = P > 4, H5 = P > 5, H6 = P > 6;
-  static_assert(P >= 3 && P <= 7, "images 7 and 8 are not projected by this kernel");
+  static constexpr bool H3 = P > 3, H4 = P > 4, H5 = P > 5, H6 = P > 6, H7 = P > 7, H8 = P > 8;
+  // the in-slice diagonal images 7 (x+y) and 8 (x-y) of one slice of a tile
+  // span DW pixels
+  static constexpr int DW = TXc + TYc - 1;
+  static_assert(P >= 3 && P <= 9, "images 9 and 10 are projected by a second kernel");
   static_assert(GB * RYB == TYc && BXB == BB, "group B covers the tile with one block column");
   static_assert(RA % BB == 0 && NBR % 8 == 0 && BYA == 2, "transposed-buffer blocks");
   static_assert(RA <= 8 && RYB == 8, "windows of up to 8 positions");
@@ -187,6 +190,10 @@ __device__ __forceinline__ void red_add(uint32_t* p, uint32_t v) {
 // without the zero test (per-step sums, which are rarely zero)
 __device__ __forceinline__ void red_add_always(uint32_t* p, uint32_t v) {
   asm volatile("red.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Shared-memory reduction (no return value).
+__device__ __forceinline__ void red_shared(uint32_t* p, uint32_t v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
 }
 __device__ __forceinline__ float max_nan(float a, float b) {
   float d;
@@ -377,7 +384,8 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
   constexpr int TXc = C::TXc, TYc = C::TYc, STAGES = C::STAGES;
   constexpr int GA = C::GA, RA = C::RA, BYA = C::BYA, RYB = C::RYB, GB = C::GB, BXB = C::BXB;
   constexpr int BB = C::BB, NBR = C::NBR, NBC = C::NBC;
-  constexpr bool H3 = C::H3, H4 = C::H4, H5 = C::H5, H6 = C::H6;
+  constexpr bool H3 = C::H3, H4 = C::H4, H5 = C::H5, H6 = C::H6, H7 = C::H7, H8 = C::H8;
+  constexpr int DW = C::DW;
   constexpr int NTRA = (32 / GA) * NWG;  // group A thread-rows
 
   // ---- shared memory (sections 128-byte aligned)
@@ -400,6 +408,12 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
   uint4* xbuf = reinterpret_cast<uint4*>(take(sizeof(uint4) * 2 * 2 * NBC * NBR));
   // image 0 sums of group B (A0SMEM), [block column][block position]
   uint4* a0buf = C::A0SMEM ? reinterpret_cast<uint4*>(take(sizeof(uint4) * NBC * NBR)) : nullptr;
+  // the step's partial diagonal rows of images 7 (group A) and 8 (group B),
+  // [buf][slice][limb][DW], merged into the images one step later
+  uint32_t* diag7 = H7 ? reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * 2 * 2 * NL * DW))
+                       : nullptr;
+  uint32_t* diag8 = H8 ? reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * 2 * 2 * NL * DW))
+                       : nullptr;
   float* red_f = reinterpret_cast<float*>(take(sizeof(float) * 32));
   int* abort_flag = reinterpret_cast<int*>(take(sizeof(int)));
 
@@ -485,6 +499,10 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
     run3[i] = 0;
     run4[i] = 0;
   }
+  if constexpr (H7)
+    for (int i = tid; i < 2 * 2 * NL * DW; i += NT) diag7[i] = 0;
+  if constexpr (H8)
+    for (int i = tid; i < 2 * 2 * NL * DW; i += NT) diag8[i] = 0;
   __syncthreads();
 
   const uint64_t policy = evict_first_policy();
@@ -503,6 +521,25 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
   // image pixel pointers (limb 0; limb l adds l * lstride)
   auto pix = [&](int k, int64_t s, int64_t f) -> uint32_t* {
     return img + set.base[k] + s * set.F[k] + f;
+  };
+  // One step's partial diagonal rows (buffer buf, z-pair at zb, tile x0, y0)
+  // into image k (7: f = x0 + y0 + d; 8: f = x0 - y0 + d - (TYc - 1) + M - 1),
+  // shared out over the 256 threads of one group (gt = thread in the group);
+  // each entry is zeroed for the buffer's next use.
+  auto merge_diag = [&](uint32_t* dg, int k, int buf, int zb, int x0, int y0, int gt) {
+    const int64_t f0 = k == 7 ? (int64_t)x0 + y0 : (int64_t)x0 - y0 - (TYc - 1) + (M - 1);
+    for (int e = gt; e < 2 * NL * DW; e += 32 * NWG) {
+      const int d = e % DW, l = (e / DW) % NL, sl = e / (DW * NL);
+      uint32_t* src = dg + ((buf * 2 + sl) * NL + l) * DW + d;
+      const uint32_t val = *src;
+      if (val) {
+        *src = 0;
+        const int64_t f = f0 + d;
+        const int zz = zb + sl;
+        if (f >= 0 && f < set.F[k] && zz < zend && zz < N)
+          red_add_always(img + set.base[k] + (int64_t)zz * set.F[k] + f + l * lstride, val);
+      }
+    }
   };
   // the block of (block row br, block column bc), slice sl, buffer buf
   auto xblk = [&](int buf, int sl, int br, int bc) -> uint4* {
@@ -582,6 +619,11 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
       }
       int z = za;
       for (int i = 0; i < nsteps; ++i) {
+        // the previous step's diagonal rows of image 7 (complete since the
+        // step barrier) into the image, while this step's copy may still land
+        if constexpr (H7) {
+          if (i > 0) merge_diag(diag7, 7, (s - 1) & 1, z - 2, x0, y0, tid);
+        }
         const int st = s % STAGES;
         const bool ok = mbar_wait_bounded(smem_u32(&mbar[st]), (uint32_t)((s / STAGES) & 1),
                                           p.wait_budget);
@@ -603,6 +645,20 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
                 for (int l = 0; l < NL; ++l) e[(ri * BB + cj) * NL + l] = v[sl][ri][BB * j + cj][l];
             xwr[sl][j][(s & 1) * 2 * NBC * NBR] = make_uint4(e[0], e[1], e[2], e[3]);
           }
+        if constexpr (H7) {
+          // image 7 (z, x+y): the micro-tile's RA + 1 diagonals (x - x0) +
+          // (y - y0) = xl + yl + k, per slice and limb, into the step's row
+#pragma unroll
+          for (int sl = 0; sl < 2; ++sl)
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+              uint32_t* row = diag7 + (((s & 1) * 2 + sl) * NL + l) * DW + xl + yl;
+              red_shared(row, v[sl][0][0][l]);
+#pragma unroll
+              for (int k = 1; k < RA; ++k) red_shared(row + k, v[sl][0][k][l] + v[sl][1][k - 1][l]);
+              red_shared(row + RA, v[sl][1][RA - 1][l]);
+            }
+        }
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
 #pragma unroll
@@ -679,6 +735,7 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
       }
       if (aborted) break;
       __syncthreads();  // group B finishes the segment's last z-pair
+      if constexpr (H7) merge_diag(diag7, 7, (s - 1) & 1, z - 2, x0, y0, tid);
       // segment end: exit runs and windows into the images
       flush_runs(yt, (int64_t)x0 + run_start, 0, 2 * run_len,
                  (int64_t)x0 + TXc - 16 - run_start + c4, 16 - 2 * run_len, 16);
@@ -787,6 +844,9 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
         }
         // the previous z-pair's edge rows
         if ((H5 || H6) && i > 0) emit_edges(buf ^ 1, z - 2, x0, y0);
+        if constexpr (H8) {
+          if (i > 0) merge_diag(diag8, 8, buf ^ 1, z - 2, x0, y0, tid - 32 * NWG);
+        }
         uint32_t v[2][RYB][BXB][NL];
 #pragma unroll
         for (int sl = 0; sl < 2; ++sl)
@@ -801,6 +861,26 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
 #pragma unroll
                 for (int l = 0; l < NL; ++l) v[sl][2 * bi + ri][cj][l] = e[(ri * BB + cj) * NL + l];
           }
+        if constexpr (H8) {
+          // image 8 (z, x-y): the micro-tile's RYB + BXB - 1 diagonals
+          // (x - x0) - (y - y0) + TYc - 1 = xl - yl - (RYB - 1) + TYc - 1 + k,
+          // per slice and limb, into the step's row
+#pragma unroll
+          for (int sl = 0; sl < 2; ++sl)
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+              uint32_t dsum[RYB + BXB - 1];
+#pragma unroll
+              for (int k = 0; k < RYB + BXB - 1; ++k) dsum[k] = 0;
+#pragma unroll
+              for (int q = 0; q < RYB; ++q)
+#pragma unroll
+                for (int c = 0; c < BXB; ++c) dsum[c - q + RYB - 1] += v[sl][q][c][l];
+              uint32_t* row = diag8 + ((buf * 2 + sl) * NL + l) * DW + xl - yl - (RYB - 1) + TYc - 1;
+#pragma unroll
+              for (int k = 0; k < RYB + BXB - 1; ++k) red_shared(row + k, dsum[k]);
+            }
+        }
 #pragma unroll
         for (int c = 0; c < BXB; ++c)
 #pragma unroll
@@ -878,6 +958,7 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
       if (aborted) break;
       __syncthreads();  // matches group A's segment-end barrier: edge rows visible
       if (H5 || H6) emit_edges((s - 1) & 1, z - 2, x0, y0);
+      if constexpr (H8) merge_diag(diag8, 8, (s - 1) & 1, z - 2, x0, y0, tid - 32 * NWG);
       // segment end: windows into the images
       const int zn = z;
 #pragma unroll
@@ -969,6 +1050,8 @@ size_t smem_bytes() {
   b += rnd(sizeof(uint32_t) * 2 * 2 * 2 * C::NL * C::TXc);
   b += rnd(sizeof(uint4) * 2 * 2 * C::NBC * C::NBR);
   if (C::A0SMEM) b += rnd(sizeof(uint4) * C::NBC * C::NBR);
+  if (C::H7) b += rnd(sizeof(uint32_t) * 2 * 2 * C::NL * C::DW);
+  if (C::H8) b += rnd(sizeof(uint32_t) * 2 * 2 * C::NL * C::DW);
   b += rnd(sizeof(float) * 32);
   b += rnd(sizeof(int));
   return b;

@@ -87,18 +87,35 @@ __global__ void clear_sample_kernel(uint4* p, int64_t n16, int* status, int* fla
 
 bool project_int_supported(const void* vol, int64_t L, int dtype, int P) {
   const int64_t es = dtype == 0 ? 1 : (dtype == 1 ? 2 : 4);
-  return P >= 3 && P <= 7 && (L * es) % 16 == 0 && (reinterpret_cast<uintptr_t>(vol) % 16) == 0;
+  // images 9 and 10 (integer volumes) come from the second kernel
+  const int Pmax = dtype == 2 ? 9 : 11;
+  return P >= 3 && P <= Pmax && (L * es) % 16 == 0 &&
+         (reinterpret_cast<uintptr_t>(vol) % 16) == 0;
 }
 
 cudaError_t launch_project_int(const IntProjectArgs& a, cudaStream_t st) {
   const int P = a.set.P;
   if (!project_int_supported(a.vol, a.L, a.dtype, P)) return cudaErrorInvalidValue;
+  const int P9 = P < 9 ? P : 9;  // images 0-8 in the fused pass
+  cudaError_t e;
   switch (a.dtype) {
-    case 0: return k1i::launch_u8(P, a, st);
-    case 1: return k1i::launch_u16(P, a, st);
-    case 2: return k1i::launch_f32(P, a, st);
+    case 0: e = k1i::launch_u8(P9, a, st); break;
+    case 1: e = k1i::launch_u16(P9, a, st); break;
+    case 2: e = k1i::launch_f32(P9, a, st); break;
     default: return cudaErrorInvalidValue;
   }
+  if (e != cudaSuccess || P <= 9) return e;
+  // images 9 and 10 of an integer volume
+  ProjectArgs pa{};
+  pa.vol = a.vol;
+  pa.L = a.L; pa.M = a.M; pa.N = a.N;
+  pa.dtype = a.dtype;
+  pa.images = a.images;
+  pa.set = a.set;
+  pa.status = a.status;
+  pa.z0 = a.z0;
+  pa.nz = a.nz;
+  return launch_project_extra(pa, st);
 }
 
 cudaError_t launch_clear_sample(void* p, size_t bytes, int* status, int* flags, const float* vol,

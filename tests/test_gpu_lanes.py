@@ -1,4 +1,5 @@
-"""GPU parity of the integer-lane projection (volumes with 16-byte aligned rows).
+"""GPU parity of the integer-lane projection (volumes with 16-byte aligned rows;
+images 0-8, with the in-slice diagonal images 7 and 8 at K = 7, 8).
 
 Integer volumes: images and moments bit for bit against the oracle.  Float32
 volumes are quantised onto two int32 limbs and projected exactly; their
@@ -53,7 +54,7 @@ SHAPES = [
 def test_lane_images_bit_exact(dpma, shape, dtype):
     vol = synth.uniform_volume(shape, dtype, seed=sum(shape) + 17)
     t, dt = dev(vol)
-    for K in (2, 3, 4, 5, 6):
+    for K in (2, 3, 4, 5, 6, 7, 8):
         got = dpma.project(t, K, dt)
         want = oracle.project(vol, oracle.num_images(K))
         for k, (g, w) in enumerate(zip(got, want)):
@@ -86,7 +87,7 @@ def test_lane_float_moments(dpma, shape, kind):
     else:
         vol = synth.uniform_volume(shape, np.float32, sum(shape))
     t, dt = dev(vol)
-    for K in (0, 1, 3, 4, 6):
+    for K in (0, 1, 3, 4, 6, 7, 8):
         got = dpma.moments_values(t, K, dt)
         assert dpma.last_float_path() == 0, f"K={K} {shape} took the fallback"
         want = oracle.moments(vol, K)
