@@ -96,6 +96,22 @@ def test_lane_float_moments(dpma, shape, kind):
         assert np.all(err <= TOL * mag), (K, shape, float(np.max(err / np.maximum(mag, 1e-300))))
 
 
+def test_lane_float_results_are_deterministic(dpma):
+    """The quantised float pipeline sums integers only, so repeated calls on
+    the same volume give bit-identical moments (no order-dependent float
+    merges), through the synchronous and the asynchronous entry points."""
+    vol = synth.mri_like_f32(96, 80, 70, seed=12, n_blobs=8)
+    t, dt = dev(vol)
+    first = dpma.moments_values(t, 6, dt)
+    assert dpma.last_float_path() == 0
+    for _ in range(3):
+        np.testing.assert_array_equal(dpma.moments_values(t, 6, dt), first)
+    out = torch.empty(dpma.num_moments(6), dtype=torch.float64, device="cuda")
+    dpma.moments_async(t, 6, out, dt)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), first)
+
+
 def test_lane_float_full_range_goes_to_fallback(dpma):
     """One voxel 2^40 times the rest: the quantisation grid that holds it
     cannot resolve the others within the tolerance, so the compensated

@@ -135,6 +135,8 @@ def test_config_512cubed_f32_mri_k6(dpma):
     vol = synth.mri_like_f32(512, 512, 512, seed=3)
     t, dt = dev(vol)
     got = dpma.moments_values(t, 6, dt)
+    # the bench workload is served by the quantised integer-lane pipeline
+    assert dpma.last_float_path() == 0
     want = oracle.moments(vol, 6)
     mag = oracle.moments(vol, 6, absolute=True)
     rel = np.abs(got - want) / mag
@@ -163,7 +165,8 @@ def test_host_path_matches_device_path(dpma):
         host = dpma.moments_host(vol.view(np.int16) if dtype == np.uint16 else vol, K, dt)
         d = dpma.moments(t, K, dt).cpu().numpy()
         if dtype == np.float32:
-            # float atomics merge partial sums in a run-dependent order
+            # the host path takes its quantisation grid from another sample
+            # of rows, so the last bits may differ
             mag = oracle.moments(vol, K, absolute=True)
             assert np.all(np.abs(host - d) <= 1e-12 * mag)
         else:
