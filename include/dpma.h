@@ -11,7 +11,7 @@
  *      pass over the voxels, with additions only (Sec. 3.1, Eqs. 4-9);
  *   2. take the 2-D moments of every image (Sec. 1, Eq. 1; Sec. 3.2);
  *   3. combine them linearly into the 3-D moments (Eqs. 10-16, generalised to
- *      any K <= 8 by an exact integer combine matrix per degree).
+ *      any K <= 10 by an exact integer combine matrix per degree).
  *
  * Conventions used by every entry point
  * -------------------------------------
