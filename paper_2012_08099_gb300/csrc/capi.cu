@@ -431,11 +431,12 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
     e = launch_clear(images, w.img_bytes, status, st);
   } else {
     // the images (rounded up to 16 bytes: the padding before the next
-    // section), the status words and, for a device-resident float volume,
-    // the magnitude sample
+    // section), the 2-D moments (step 2 adds into them), the status words
+    // and, for a device-resident float volume, the magnitude sample
     e = launch_clear_sample(images, align_up(w.img_bytes, 16), status, flags,
                             fl && !host_src ? static_cast<const float*>(volume) : nullptr, L, M,
-                            0, N, fl && !host_src ? sample : nullptr, &ia_nsample, st);
+                            0, N, fl && !host_src ? sample : nullptr, &ia_nsample, st, 0,
+                            ws + w.off_m2d, align_up(w.m2d_bytes, 16));
   }
   if (e != cudaSuccess) return cuda_fail(e, "clear images");
   rec.mark(0, 1);
@@ -522,9 +523,9 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
   rec.mark(1, k1_launches);
   if (lanes && fl) {
     e = launch_image_moments_limbs(images, w.set, w.set.total_elems, K, 2, ws + w.off_part,
-                                   ws + w.off_m2d, st);
+                                   ws + w.off_m2d, st, true);
     if (e != cudaSuccess) return cuda_fail(e, "image moment kernel");
-    rec.mark(2, 2);
+    rec.mark(2, 1);
     e = launch_combine_fixed(ws + w.off_m2d, K, w.set.P, static_cast<double*>(out), status, flags,
                              scale, L, M, N, kFloatTolerance, st);
     if (e != cudaSuccess) return cuda_fail(e, "combine kernel");
@@ -536,9 +537,12 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
     rec.mark(3, 1 + fb_launches);
     return fs;
   }
-  e = launch_image_moments(images, w.set, K, fl, ws + w.off_part, ws + w.off_m2d, st);
+  // on the integer-lane path the clear above zeroed the 2-D moments, so the
+  // image moment kernel accumulates them itself (no reduction launch)
+  e = launch_image_moments(images, w.set, K, fl, ws + w.off_part, ws + w.off_m2d, st, nullptr,
+                           lanes && !fl);
   if (e != cudaSuccess) return cuda_fail(e, "image moment kernel");
-  rec.mark(2, 2);
+  rec.mark(2, lanes && !fl ? 1 : 2);
   e = launch_combine(ws + w.off_m2d, K, fl, out, status, st);
   if (e != cudaSuccess) return cuda_fail(e, "combine kernel");
   rec.mark(3, 1);

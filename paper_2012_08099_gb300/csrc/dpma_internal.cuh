@@ -135,15 +135,16 @@ struct IntProjectArgs {
 // and at most 7 images).
 bool project_int_supported(const void* vol, int64_t L, int dtype, int P);
 cudaError_t launch_project_int(const IntProjectArgs& a, cudaStream_t st);
-// Zeroes `bytes` at p (16-byte aligned, a multiple of 16), the status and
-// flags words, and for float volumes (sample != null) writes into
+// Zeroes `bytes` at p (16-byte aligned, a multiple of 16), as many at p2
+// (same rules; may be null), the status and flags words, and for float volumes (sample != null) writes into
 // sample[0 .. nsample) the maxima of |v| over a sample of rows of slices
 // z0 .. z0 + nz - 1: about 4096 rows spread over them, or, with row_stride
 // > 0, exactly the rows 0, row_stride, 2 row_stride, ... (row r = z * M + y
 // counted from slice z0).  Returns the sample length through *nsample.
 cudaError_t launch_clear_sample(void* p, size_t bytes, int* status, int* flags, const float* vol,
                                 int64_t L, int64_t M, int64_t z0, int64_t nz, uint32_t* sample,
-                                int* nsample, cudaStream_t st, int64_t row_stride = 0);
+                                int* nsample, cudaStream_t st, int64_t row_stride = 0,
+                                void* p2 = nullptr, size_t bytes2 = 0);
 constexpr int kMaxSample = 2048;  // sample slots
 
 // Step 2 by the discrete Radon route (k2_drt.cu): integer images only.
@@ -156,18 +157,21 @@ int drt_direction(int j, int* alpha, int* beta);
 bool drt_plan_degree(int n, int64_t* E, int64_t* D);
 
 // Step 2: block partials of every image's 2-D moments into `partials`
-// (int128 or float pairs), then a reduction into `m2d`.
+// (int128 or float pairs), then a reduction into `m2d`.  For integer images
+// whose `m2d` the caller has zeroed on the same stream (m2d_zeroed), each
+// block adds its sums into `m2d` itself and the reduction launch is skipped.
 size_t moments2d_partials_bytes(const ImageSet& set, int K, bool is_float);
 cudaError_t launch_image_moments(const void* images, const ImageSet& set, int K, bool is_float,
                                  void* partials, void* m2d, cudaStream_t st,
-                                 const int* gate = nullptr);
+                                 const int* gate = nullptr, bool m2d_zeroed = false);
 // Step 2 on nl limb sets of int32 images (image i of the nl * P is image
 // i % P of limb i / P, at base[i % P] + (i / P) * limb_stride); `m2d`
 // receives nl * P rows of int128 moments.
 constexpr int kMaxLimbImages = 2 * kMaxImages;
 size_t moments2d_partials_bytes_limbs(const ImageSet& set, int K, int nl);
 cudaError_t launch_image_moments_limbs(const void* images, const ImageSet& set, int64_t limb_stride,
-                                       int K, int nl, void* partials, void* m2d, cudaStream_t st);
+                                       int K, int nl, void* partials, void* m2d, cudaStream_t st,
+                                       bool m2d_zeroed = false);
 
 // Step 3: combine into 3-D moments.
 cudaError_t launch_combine(const void* m2d, int K, bool is_float, void* out, int* status,

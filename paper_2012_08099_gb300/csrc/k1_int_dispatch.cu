@@ -32,7 +32,8 @@ namespace {
 // b, b + G, ... of the float volume (row j of the sample is volume row
 // j * rows / nsr, jittered inside its stride) and stores the largest |v|
 // it saw (float bits; NaN propagates) in sample[b].
-__global__ void clear_sample_kernel(uint4* p, int64_t n16, int* status, int* flags,
+__global__ void clear_sample_kernel(uint4* p, int64_t n16, uint4* p2, int64_t n2,
+                                    int* status, int* flags,
                                     const float* vol, int64_t L, int64_t M, int64_t z0,
                                     int64_t nz, uint32_t* sample, int64_t nsr,
                                     int64_t row_stride) {
@@ -43,6 +44,7 @@ __global__ void clear_sample_kernel(uint4* p, int64_t n16, int* status, int* fla
     if (flags) *flags = 0;
   }
   for (int64_t i = gid; i < n16; i += stride) p[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int64_t i = gid; i < n2; i += stride) p2[i] = make_uint4(0u, 0u, 0u, 0u);
   if (!sample) return;
   const int64_t rows = M * nz;
   const int64_t step = rows / nsr;  // >= 1
@@ -120,8 +122,10 @@ cudaError_t launch_project_int(const IntProjectArgs& a, cudaStream_t st) {
 
 cudaError_t launch_clear_sample(void* p, size_t bytes, int* status, int* flags, const float* vol,
                                 int64_t L, int64_t M, int64_t z0, int64_t nz, uint32_t* sample,
-                                int* nsample, cudaStream_t st, int64_t row_stride) {
+                                int* nsample, cudaStream_t st, int64_t row_stride, void* p2,
+                                size_t bytes2) {
   if ((reinterpret_cast<uintptr_t>(p) & 15) != 0 || (bytes & 15) != 0) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(p2) & 15) != 0 || (bytes2 & 15) != 0) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -143,7 +147,8 @@ cudaError_t launch_clear_sample(void* p, size_t bytes, int* status, int* flags, 
   if (blocks < 1) blocks = 1;
   if (nsample) *nsample = sample ? (int)blocks : 0;
   k1i::clear_sample_kernel<<<(unsigned)blocks, 256, 0, st>>>(
-      static_cast<uint4*>(p), n16, status, flags, vol, L, M, z0, nz, sample, nsr, row_stride);
+      static_cast<uint4*>(p), n16, static_cast<uint4*>(p2), p2 ? (int64_t)(bytes2 / 16) : 0,
+      status, flags, vol, L, M, z0, nz, sample, nsr, row_stride);
   return cudaGetLastError();
 }
 

@@ -33,7 +33,22 @@ struct K2Params {
   int64_t blk_base[kMaxLimbImages + 1];  // first block of each image; [nimg] = total
   void* partials;                        // [block][npairs] int128 or float2
   const int* gate;                       // fallback launch: nothing unless (*gate & 3)
+  // integer images: when set, each CTA adds its sums into these zeroed
+  // [nimg][npairs] int128 moments itself and no reduction launch follows
+  i128* m2d_atomic;
 };
+
+// dst += v modulo 2^128 with two 64-bit atomic adds: the low word's carry,
+// known from its value before the add, goes into the high word, so any
+// interleaving of such adds leaves the exact sum.
+__device__ __forceinline__ void atomic_add_u128(i128* dst, u128 v) {
+  unsigned long long* w = reinterpret_cast<unsigned long long*>(dst);
+  const unsigned long long lo = (unsigned long long)v;
+  const unsigned long long hi = (unsigned long long)(v >> 64);
+  const unsigned long long old = atomicAdd(w, lo);
+  const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+  if (hi + carry) atomicAdd(w + 1, hi + carry);
+}
 
 // Integer images by cascaded sums -------------------------------------------
 //
@@ -186,7 +201,8 @@ __global__ void __launch_bounds__(kUnitThreads) k2_int_cascade_kernel(K2Params p
     const int b = j - n * (n + 1) / 2, a = n - b;
     u128 acc = 0;
     for (int c = 0; c < CH; ++c) acc += part[b][c][a];
-    static_cast<i128*>(p.partials)[(int64_t)blk * p.npairs + j] = (i128)acc;
+    if (p.m2d_atomic) atomic_add_u128(p.m2d_atomic + (int64_t)kk * p.npairs + j, acc);
+    else static_cast<i128*>(p.partials)[(int64_t)blk * p.npairs + j] = (i128)acc;
   }
 }
 
@@ -377,9 +393,12 @@ cudaError_t launch_reduce_partials(const void* partials, const int64_t* blk_base
 
 namespace {
 cudaError_t launch_k2(const void* images, const ImageSet& set, int K, bool is_float, int nl,
-                      bool sgn, void* partials, void* m2d, cudaStream_t st, const int* gate) {
+                      bool sgn, void* partials, void* m2d, cudaStream_t st, const int* gate,
+                      bool m2d_zeroed) {
   K2Params p{};
   p.gate = gate;
+  const bool atomic = m2d_zeroed && !is_float;
+  p.m2d_atomic = atomic ? static_cast<i128*>(m2d) : nullptr;
   p.images = images;
   p.set = set;
   p.nimg = nl * set.P;
@@ -410,21 +429,23 @@ cudaError_t launch_k2(const void* images, const ImageSet& set, int K, bool is_fl
     default: return cudaErrorInvalidValue;
   }
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || atomic) return e;
   return launch_reduce_partials(partials, p.blk_base, p.nimg, K, is_float, m2d, st, gate);
 }
 }  // namespace
 
 cudaError_t launch_image_moments(const void* images, const ImageSet& set, int K, bool is_float,
-                                 void* partials, void* m2d, cudaStream_t st, const int* gate) {
-  return launch_k2(images, set, K, is_float, 1, false, partials, m2d, st, gate);
+                                 void* partials, void* m2d, cudaStream_t st, const int* gate,
+                                 bool m2d_zeroed) {
+  return launch_k2(images, set, K, is_float, 1, false, partials, m2d, st, gate, m2d_zeroed);
 }
 
 cudaError_t launch_image_moments_limbs(const void* images, const ImageSet& set, int64_t limb_stride,
-                                       int K, int nl, void* partials, void* m2d, cudaStream_t st) {
+                                       int K, int nl, void* partials, void* m2d, cudaStream_t st,
+                                       bool m2d_zeroed) {
   ImageSet s2 = set;
   s2.total_elems = limb_stride;  // the kernel steps from limb to limb by total_elems
-  return launch_k2(images, s2, K, false, nl, true, partials, m2d, st, nullptr);
+  return launch_k2(images, s2, K, false, nl, true, partials, m2d, st, nullptr, m2d_zeroed);
 }
 
 }  // namespace dpma
