@@ -1278,6 +1278,7 @@ dpma_status dpma_batch_create(const dpma_volume_desc* descs, int count, int flag
 
 dpma_status dpma_batch_run(dpma_batch* plan, void* out, void* stream) {
   if (!plan || !out) return bfail(DPMA_ERR_INVALID_ARG, "null plan or output pointer");
+  const NvtxRange range("dpma: batch run");
   return enqueue_batch(plan, out, static_cast<cudaStream_t>(stream));
 }
 

@@ -413,6 +413,7 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
                     void* out, cudaStream_t st, unsigned char* ws, const Layout& w,
                     const void* host_src = nullptr, cudaStream_t copy_st = nullptr,
                     cudaEvent_t ev = nullptr) {
+  const NvtxRange range("dpma: moments");
   cudaError_t e = prepare_combine(K);
   if (e != cudaSuccess) return cuda_fail(e, "combine plan");
   StageRecorder rec(st);
@@ -591,6 +592,7 @@ dpma_status enqueue_device(const void* volume, int64_t L, int64_t M, int64_t N, 
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   const bool capturing = cudaStreamIsCapturing(st, &cs) == cudaSuccess &&
                          cs != cudaStreamCaptureStatusNone;
+  const NvtxRange range("dpma: pipeline call");
   PipeKey k{};
   if (timing || capturing || cudaGetDevice(&k.dev) != cudaSuccess)
     return enqueue(volume, L, M, N, dtype, K, out, st, ws, w);

@@ -3,10 +3,20 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "plan.h"
 
 namespace dpma {
+
+// A named range on the host timeline of a profiler (NVTX), for the scope of
+// the object; costs a pointer test when no profiler is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 using i128 = __int128;
 using u128 = unsigned __int128;

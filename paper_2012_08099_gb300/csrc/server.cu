@@ -586,6 +586,7 @@ void scheduler(dpma_server* s) {
         continue;
       }
       // admission in arrival order while a slot and device memory are free
+      const NvtxRange admit_range("dpma: server admission");
       while (!s->pending.empty() && s->inflight + (int)admitted.size() < s->cfg.max_inflight) {
         Request* r = s->pending.front();
         CacheEntry* hit = find_entry(s, r);
@@ -742,6 +743,7 @@ dpma_status dpma_server_submit_keyed(dpma_server* s, const dpma_volume_desc* des
                                      uint64_t* ticket) {
   // latency runs from entry to this call (before the pinned copy) to completion
   const double t_entry = now_ms();
+  const NvtxRange range("dpma: server submit");
   if (!s || !desc || !ticket) return sfail(DPMA_ERR_INVALID_ARG, "null argument");
   dpma_volume_desc d = *desc;
   d.out_offset = 0;
