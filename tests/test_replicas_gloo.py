@@ -67,3 +67,87 @@ def test_two_gloo_replicas():
         assert ok, f"rank {rank}: replica moments differ from the oracle"
         assert worst == 2.0
         assert rate == pytest.approx(2 * nvox / 2.0e-3)
+
+
+def _slab_rank(rank: int, world: int, port: int, out):
+    """One z-slab of a volume per rank: local moments, shifted to the volume's
+    z origin (binomial expansion of (z' + z0)^r), summed over the ranks by
+    one collective; rank 0 reports the sum."""
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from math import comb
+
+        import cpu_dpma
+        import oracle
+        from paper_2012_08099_gb300 import synth
+        vol = synth.uniform_volume((23, 11, 16), np.uint16, seed=7)
+        K = 5
+        h = 10  # rank 0: z < h, rank 1: z >= h
+        z0 = 0 if rank == 0 else h
+        slab = vol[:h] if rank == 0 else vol[h:]
+        local = list(cpu_dpma.moments(np.ascontiguousarray(slab), K, threads=2))
+        idx = {tr: i for i, tr in enumerate(oracle.graded_triples(K))}
+        shifted = [0] * len(local)
+        for (p, q, r), i in idx.items():
+            shifted[i] = sum(comb(r, k) * z0 ** (r - k) * local[idx[(p, q, k)]]
+                             for k in range(r + 1))
+        parts = [None] * world
+        dist.all_gather_object(parts, shifted)
+        if rank == 0:
+            total = [sum(col) for col in zip(*parts)]
+            out.put(total == list(oracle.moments(vol, K, nthreads=1)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_split_one_volume():
+    """The other way the method shards (one large volume cut along z): each
+    rank computes its slab, the moments are exact integers, so one sum over
+    the ranks gives the volume's moments bit for bit."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_slab_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    ok = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert ok
+
+
+def _dead_peer_rank(rank: int, world: int, port: int, out):
+    """Rank 1 leaves before the collective; rank 0's collective must end with
+    an error after the process group's short timeout instead of hanging."""
+    import datetime
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=5))
+    if rank == 1:
+        os._exit(0)  # dies without joining the collective
+    t = torch.ones(4)
+    try:
+        dist.all_reduce(t)
+        out.put("completed")
+    except Exception as e:  # the dead peer is detected
+        out.put("error: " + type(e).__name__)
+
+
+def test_dead_rank_is_detected_on_the_host():
+    """Failure detection without a GPU fault: a rank that dies between steps
+    makes the survivor's next collective fail after its timeout."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dead_peer_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+        if p.is_alive():
+            p.kill()
+    assert res.startswith("error"), res
