@@ -97,6 +97,14 @@ typedef struct {
     int overflow; /* set if any product or sum left the int128 range */
 } int_job;
 
+/* pw[e] = c^e for e = 0..K; returns 1 if one of them leaves the int128 range. */
+static int checked_powers(i128* pw, int64_t c, int K) {
+    pw[0] = 1;
+    for (int e = 1; e <= K; ++e)
+        if (__builtin_mul_overflow(pw[e - 1], (i128)c, &pw[e])) return 1;
+    return 0;
+}
+
 static uint32_t load_int(const void* vol, int elem_bytes, int64_t idx) {
     if (elem_bytes == 1) return ((const uint8_t*)vol)[idx];
     return ((const uint16_t*)vol)[idx];
@@ -108,16 +116,19 @@ static void* int_worker(void* arg) {
     i128 xp[ORACLE_MAX_K + 1], yp[ORACLE_MAX_K + 1], zp[ORACLE_MAX_K + 1];
     for (int m = 0; m < J->nmom; ++m) J->acc[m] = 0;
     for (int64_t z = J->z0; z < J->z1; ++z) {
-        zp[0] = 1;
-        for (int e = 1; e <= K; ++e) zp[e] = zp[e - 1] * (i128)z;
+        int zov = checked_powers(zp, z, K);
         for (int64_t y = 0; y < J->M; ++y) {
-            yp[0] = 1;
-            for (int e = 1; e <= K; ++e) yp[e] = yp[e - 1] * (i128)y;
+            int yov = checked_powers(yp, y, K);
             for (int64_t x = 0; x < J->L; ++x) {
                 uint32_t v = load_int(J->vol, J->elem_bytes, (z * J->M + y) * J->L + x);
                 if (v == 0) continue; /* a zero voxel adds nothing to Eq. 2 */
-                xp[0] = 1;
-                for (int e = 1; e <= K; ++e) xp[e] = xp[e - 1] * (i128)x;
+                /* Coordinates are non-negative, so every term is too and a power
+                 * c^e past the int128 range makes the moment with that single
+                 * exponent (e, 0, 0), (0, e, 0) or (0, 0, e) overflow as well. */
+                if (checked_powers(xp, x, K) || yov || zov) {
+                    J->overflow = 1;
+                    return NULL;
+                }
                 for (int m = 0; m < J->nmom; ++m) {
                     const int* t = J->trip + 3 * m;
                     i128 term, a, b;
@@ -146,7 +157,7 @@ int oracle_moments_int(const void* vol, int elem_bytes, int64_t L, int64_t M, in
                        int nthreads, int64_t* out) {
     if (!vol || !out || L < 1 || M < 1 || N < 1 || K < 0 || K > ORACLE_MAX_K) return 1;
     if (elem_bytes != 1 && elem_bytes != 2) return 1;
-    if (L > 32768 || M > 32768 || N > 32768) return 1;
+    if (L > 65536 || M > 65536 || N > 65536) return 1;
     if (nthreads < 1) nthreads = 1;
     if (nthreads > N) nthreads = (int)N;
     int nmom = oracle_num_moments(K);

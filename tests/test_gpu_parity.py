@@ -222,6 +222,32 @@ def test_z_slab_additivity_at_full_size(dpma):
         assert whole[i] == lo[i] + shifted
 
 
+@pytest.mark.parametrize("shape,dtype,K,full", [
+    ((2, 3, 65536), np.uint16, 4, True),   # x-lines of 65536 voxels at 65535: pixel sums
+                                           # 65536 * 65535, the top of the uint32 range
+    ((65536, 1, 16), np.uint8, 3, False),  # z-lines of 65536 slices, one row per slice
+    ((3, 65536, 16), np.uint16, 4, False), # 65536 rows
+    ((2, 2, 65536), np.float32, 4, False), # float32 at the largest dimension
+])
+def test_largest_dimensions(dpma, shape, dtype, K, full):
+    """Maximum sizes: dimensions at the 65536 limit on each axis, and (first
+    case) every voxel at the type's maximum, so the longest line sum is
+    65536 * 65535 < 2^32: integers bit for bit, float32 within the
+    tolerance."""
+    if full:
+        vol = np.full(shape, np.iinfo(dtype).max, dtype=dtype)
+    else:
+        vol = make(shape, dtype, seed=sum(shape) % 1000)
+    t, dt = dev(vol)
+    got = dpma.moments_values(t, K, dt)
+    want = oracle.moments(vol, K)
+    if dtype == np.float32:
+        mag = oracle.moments(vol, K, absolute=True)
+        assert np.all(np.abs(got - want) <= FLOAT_MOMENT_TOL * mag)
+    else:
+        assert got == want
+
+
 def test_invalid_arguments(dpma):
     t = torch.zeros((4, 4, 4), dtype=torch.uint8, device="cuda")
     with pytest.raises(dpma.DpmaError) as e:

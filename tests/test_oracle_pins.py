@@ -292,3 +292,24 @@ def test_int128_overflow_is_detected_k10():
     with pytest.raises(OverflowError):
         oracle.moments(vol, 9)
     assert oracle.moments(vol, 8)[oracle.graded_triples(8).index((8, 0, 0))] == 65535 * 8191 ** 8
+
+
+def test_coordinate_power_overflow_is_detected():
+    """x^10 for x = 65535 leaves the int128 range on its own (x^7 does not);
+    the moment (10, 0, 0) of that voxel then overflows too."""
+    vol = np.zeros((1, 1, 65536), dtype=np.uint8)
+    vol[0, 0, 65535] = 1
+    with pytest.raises(OverflowError):
+        oracle.moments(vol, 10)
+    assert oracle.moments(vol, 7)[oracle.graded_triples(7).index((7, 0, 0))] == 65535 ** 7
+
+
+@pytest.mark.parametrize("shape", [(1, 2, 65536), (2, 65536, 1), (65536, 1, 2)])
+def test_constant_box_closed_form_at_largest_dimension(shape):
+    N, M, L = shape
+    vol = np.full(shape, 65535, dtype=np.uint16)
+    got = oracle.moments(vol, 4, nthreads=4)
+    for (p, q, r), g in zip(oracle.graded_triples(4), got):
+        assert g == 65535 * faulhaber(p, L) * faulhaber(q, M) * faulhaber(r, N), (p, q, r)
+    with pytest.raises(ValueError):
+        oracle.moments(np.zeros((1, 1, 65537), np.uint8), 2)
