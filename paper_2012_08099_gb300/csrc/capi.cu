@@ -340,9 +340,72 @@ cudaError_t build_fallback_graph(const FallbackKey& k, cudaStream_t cap, const L
   return cudaSuccess;
 }
 
-// Enqueues the fallback on st: the cached graph of this key, else (building
-// it on a key's second use) the plain gated launches.  *launches receives the
-// kernel launches issued from the host.
+// The fallback into a graph that st is capturing: the gate kernel, then an
+// IF node whose body is the five launches (captured on a stream of its own),
+// so a replay of the captured graph runs one gate kernel instead of five
+// gated launches while the gate is closed.
+dpma_status capture_fallback_conditional(const void* volume, int64_t L, int64_t M, int64_t N,
+                                         int K, void* out, cudaStream_t st, unsigned char* ws,
+                                         const Layout& w, int* launches) {
+  *launches = 1;
+  // the body's stream first: without it the graph stays as it is and the
+  // plain gated launches go into the capture
+  cudaStream_t side = nullptr;
+  if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    *launches = 5;
+    return enqueue_float_fallback(volume, L, M, N, K, out, st, ws, w);
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t cg = nullptr;
+  auto fail = [&](cudaError_t err, const char* where) {
+    cudaStreamDestroy(side);
+    return cuda_fail(err, where);
+  };
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, nullptr, nullptr, nullptr);
+  if (e != cudaSuccess) return fail(e, "capture info (fallback)");
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, cg, 0, 0);
+  if (e != cudaSuccess) return fail(e, "conditional handle (fallback)");
+  const int* flags = reinterpret_cast<const int*>(ws + w.off_status) + 1;
+  fallback_gate_kernel<<<1, 1, 0, st>>>(flags, h);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(e, "fallback gate kernel");
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return fail(e, "capture info (fallback)");
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeIf;
+  np.conditional.size = 1;
+  cudaGraphNode_t cond;
+  e = cudaGraphAddNode(&cond, cg, deps, nullptr, nd, &np);
+  if (e != cudaSuccess) return fail(e, "conditional node (fallback)");
+  e = cudaStreamBeginCaptureToGraph(side, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal);
+  dpma_status fs = DPMA_OK;
+  if (e == cudaSuccess) {
+    fs = enqueue_float_fallback(volume, L, M, N, K, out, side, ws, w);
+    cudaGraph_t body = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(side, &body);
+    if (e2 != cudaSuccess && fs == DPMA_OK) fs = cuda_fail(e2, "capture (fallback body)");
+  } else {
+    fs = cuda_fail(e, "capture (fallback body)");
+  }
+  cudaStreamDestroy(side);
+  if (fs != DPMA_OK) return fs;
+  e = cudaStreamUpdateCaptureDependencies(st, &cond, nullptr, 1,
+                                          cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) return cuda_fail(e, "capture dependencies (fallback)");
+  return DPMA_OK;
+}
+
+// Enqueues the fallback on st: inside a stream capture the conditional form
+// above; otherwise the cached graph of this key, else (building it on a key's
+// second use) the plain gated launches.  *launches receives the kernel
+// launches issued from the host.
 dpma_status enqueue_fallback(const void* volume, int64_t L, int64_t M, int64_t N, int K,
                              void* out, cudaStream_t st, unsigned char* ws, const Layout& w,
                              int* launches) {
@@ -352,7 +415,8 @@ dpma_status enqueue_fallback(const void* volume, int64_t L, int64_t M, int64_t N
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   const bool capturing = cudaStreamIsCapturing(st, &cs) == cudaSuccess &&
                          cs != cudaStreamCaptureStatusNone;
-  if (k.dev >= 0 && !capturing) {
+  if (capturing) return capture_fallback_conditional(volume, L, M, N, K, out, st, ws, w, launches);
+  if (k.dev >= 0) {
     std::lock_guard<std::mutex> lk(g_fb_mu);
     cudaGraphExec_t exec = nullptr;
     for (size_t i = 0; i < g_fb_graphs.size(); ++i)

@@ -8,7 +8,7 @@
 // each image (its DRT listing); on a GPU the separable power sums above are
 // cheaper and exact, and they give identical results.
 //
-// Integer images: one thread per row segment of 16-128 pixels runs
+// Integer images: one thread per row segment of 16-64 pixels runs
 // cascaded sums (additions only) and converts them exactly to the
 // segment's power sums F_b; the CTA then folds s^a F_b over its segments.
 // Float images (doubles): the same segments; each double is split into a
@@ -63,8 +63,16 @@ __device__ __forceinline__ void atomic_add_u128(i128* dst, u128 v) {
 // shift.  Every step is a ring operation, so all of it is exact modulo
 // 2^128, and the 2-D moments, which fit in int128, come out exact.  Per pixel
 // this costs K + 1 additions instead of K products.
-constexpr int kSegLenMax = 128;    // pixels per segment at most: A_0 .. A_4 fit in 64 bits
+// Pixels per segment at most.  A_j <= max|I| * C(n + j, j + 1), which for n = 64
+// and |I| < 2^32 stays below 2^63 up to j = 6: A_0 .. A_6 run in 64 bits.
+constexpr int kSegLenMax = 64;
+constexpr int kCascade64 = 7;  // cascade sums kept in 64 bits
 constexpr int kUnitThreads = 128;  // segments per CTA
+// The segments of one CTA are consecutive in memory (rows follow each other),
+// so the CTA first copies its pixels, at most kUnitThreads * kSegLenMax, into
+// shared memory with coalesced loads; pixel i goes to word i + i / seg, which
+// keeps the threads' sequential reads of their own segments on distinct banks.
+constexpr int kStageWords = kUnitThreads * kSegLenMax + kUnitThreads;
 
 __constant__ StirlingTable c_stirling = make_stirling();
 
@@ -87,52 +95,127 @@ __global__ void __launch_bounds__(kUnitThreads) k2_int_cascade_kernel(K2Params p
       static_cast<const uint32_t*>(p.images) + p.set.base[k] + limb * p.set.total_elems;
   const int t = threadIdx.x;
 
-  __shared__ u128 Fs[kUnitThreads][NB];  // row power sums of each segment
-  __shared__ int64_t Cs[kUnitThreads];   // its signed row coordinate
-  __shared__ u128 part[NB][CH][NB];      // fold partials [b][chunk][a]
+  // the staged pixels, and after the cascades the segments' power sums and
+  // the fold partials in the same memory
+  struct Sums {
+    u128 Fs[kUnitThreads][NB];  // row power sums of each segment
+    u128 part[NB][CH][NB];      // fold partials [b][chunk][a]
+  };
+  __shared__ union Smem {
+    uint32_t stage[kStageWords];
+    Sums sums;
+  } sm;
+  __shared__ int64_t Cs[kUnitThreads];  // each segment's signed row coordinate
+  auto& Fs = sm.sums.Fs;
+  auto& part = sm.sums.part;
+
+  // 0. the CTA's pixels into shared memory (segments of more than 16
+  // pixels; shorter ones, which only small image sets use, are read in
+  // place, where the extra copy phase would only add latency)
+  const bool staged = seg > 16;
+  const int64_t units = S * nseg;
+  const int64_t u_first = chunk * kUnitThreads;
+  const int64_t u_last = (u_first + kUnitThreads < units ? u_first + kUnitThreads : units) - 1;
+  const int lgseg = 31 - __clz((int)seg);  // seg is a power of two
+  int64_t p0, plen;
+  {
+    const int64_t s0 = u_first / nseg, sl = u_last / nseg;
+    const int64_t gl = u_last - sl * nseg;
+    p0 = s0 * F + (u_first - s0 * nseg) * seg;
+    plen = sl * F + ((gl + 1) * seg < F ? (gl + 1) * seg : F) - p0;
+  }
+  if (staged) {
+    // pixels up to the first 16-byte boundary and after the last one one by
+    // one, the rest as 16-byte loads, all issued before they are stored
+    const uint32_t* src = img + p0;
+    int head = (int)((16 - (reinterpret_cast<uintptr_t>(src) & 15)) & 15) / 4;
+    if (head > plen) head = (int)plen;
+    const int nvec = (int)((plen - head) / 4);
+    const int tail0 = head + 4 * nvec;
+    auto put = [&](int i, uint32_t v) { sm.stage[i + (i >> lgseg)] = v; };
+    if (t < head) put(t, __ldg(src + t));
+    if (tail0 + t < plen) put(tail0 + t, __ldg(src + tail0 + t));
+    const uint4* vsrc = reinterpret_cast<const uint4*>(src + head);
+    constexpr int kVecPerThread = kSegLenMax / 4;  // nvec <= kUnitThreads * kSegLenMax / 4
+    constexpr int kBatch = 8;
+#pragma unroll
+    for (int j0 = 0; j0 < kVecPerThread; j0 += kBatch) {
+      uint4 q[kBatch];
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int vi = t + (j0 + j) * kUnitThreads;
+        if (vi < nvec) q[j] = __ldg(vsrc + vi);
+      }
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int vi = t + (j0 + j) * kUnitThreads;
+        if (vi < nvec) {
+          const int i = head + 4 * vi;
+          put(i, q[j].x);
+          put(i + 1, q[j].y);
+          put(i + 2, q[j].z);
+          put(i + 3, q[j].w);
+        }
+      }
+    }
+  }
+  __syncthreads();
 
   // 1. one segment per thread
-  const int64_t u = chunk * kUnitThreads + t;
+  const int64_t u = u_first + t;
   u128 Fb[NB];
 #pragma unroll
   for (int b = 0; b < NB; ++b) Fb[b] = 0;
   int64_t cs = 0;
-  if (u < S * nseg) {
+  if (u < units) {
     const int64_t s = u / nseg, g = u - s * nseg;
     const int64_t fs = g * seg;
     const int n = (int)(F - fs < seg ? F - fs : seg);
+    const int o = (int)(s * F + fs - p0);  // the segment's first pixel in the stage
     const uint32_t* row = img + s * F + fs;
-    constexpr int N64 = NB < 5 ? NB : 5;  // A_0 .. A_4 in 64 bits
+    constexpr int N64 = NB < kCascade64 ? NB : kCascade64;  // A_0 .. A_6 in 64 bits
+    constexpr int N128 = NB > kCascade64 ? NB - kCascade64 : 1;
     uint64_t a64[N64];
-    u128 a128[NB > 5 ? NB - 5 : 1];
+    u128 a128[N128];
 #pragma unroll
     for (int j = 0; j < N64; ++j) a64[j] = 0;
 #pragma unroll
-    for (int j = 0; j < (NB > 5 ? NB - 5 : 1); ++j) a128[j] = 0;
+    for (int j = 0; j < N128; ++j) a128[j] = 0;
     auto step = [&](uint32_t px) {
       a64[0] += SGN ? (uint64_t)(int64_t)(int32_t)px : (uint64_t)px;
 #pragma unroll
       for (int j = 1; j < N64; ++j) a64[j] += a64[j - 1];
-      if constexpr (NB > 5) {
-        a128[0] += (u128)(i128)(int64_t)a64[4];
+      if constexpr (NB > kCascade64) {
+        a128[0] += (u128)(i128)(int64_t)a64[kCascade64 - 1];
 #pragma unroll
-        for (int j = 1; j < NB - 5; ++j) a128[j] += a128[j - 1];
+        for (int j = 1; j < NB - kCascade64; ++j) a128[j] += a128[j - 1];
       }
     };
-    // eight loads in flight before their eight dependent cascade steps
-    int i = 0;
-    for (; i + 8 <= n; i += 8) {
-      uint32_t q[8];
+    // eight loads ahead of their eight dependent cascade steps
+    auto cascade = [&](auto pixel) {
+      int i = 0;
+      for (; i + 8 <= n; i += 8) {
+        uint32_t q[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) q[u] = __ldg(row + i + u);
+        for (int j = 0; j < 8; ++j) q[j] = pixel(i + j);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) step(q[u]);
+        for (int j = 0; j < 8; ++j) step(q[j]);
+      }
+      for (; i < n; ++i) step(pixel(i));
+    };
+    if (staged) {
+      cascade([&](int i) -> uint32_t {
+        const int w = o + i;
+        return sm.stage[w + (w >> lgseg)];
+      });
+    } else {
+      cascade([&](int i) -> uint32_t { return __ldg(row + i); });
     }
-    for (; i < n; ++i) step(__ldg(row + i));
     u128 A[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j)
-      A[j] = j < 5 ? (u128)(i128)(int64_t)a64[j < 5 ? j : 0] : a128[j >= 5 ? j - 5 : 0];
+      A[j] = j < kCascade64 ? (u128)(i128)(int64_t)a64[j < kCascade64 ? j : 0]
+                            : a128[j >= kCascade64 ? j - kCascade64 : 0];
     // Q_b = sum_j (-1)^(b-j) S(b,j) j! A_j, then the shift to c = D - w:
     // with m_k = (-1)^k Q_k, F_b = sum_k C(b,k) D^(b-k) m_k, built by the
     // Pascal recurrence m_b += D m_(b-1) applied K times
@@ -150,6 +233,7 @@ __global__ void __launch_bounds__(kUnitThreads) k2_int_cascade_kernel(K2Params p
       for (int b = NB - 1; b >= i; --b) Fb[b] += D * Fb[b - 1];
     cs = s - off_s;
   }
+  __syncthreads();  // every cascade has read the stage, which Fs overwrites
 #pragma unroll
   for (int b = 0; b < NB; ++b) Fs[t][b] = Fb[b];
   Cs[t] = cs;
@@ -349,7 +433,7 @@ __global__ void __launch_bounds__(kUnitThreads) k2_f32_seg_kernel(K2Params p) {
   }
 }
 
-// Pixels per row segment: 16 .. 128, the largest power of two that still
+// Pixels per row segment: 16 .. 64, the largest power of two that still
 // gives about 78 K segments (16 warps per SM) over all images of all nl limb
 // sets (measured at 512^3, K = 6: float32 limbs 46.7 -> 37.5 us with the
 // eight-load prefetch, uint16 28.7 -> 27.0 us).

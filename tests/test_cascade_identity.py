@@ -7,8 +7,10 @@ second kind), and the Pascal recurrence m_b += D m_(b-1), applied K times
 to m_k = (-1)^k Q_k, yields sum (D - w)^b I, the power sums in the signed
 coordinate c = f - off_f with D = f_start + n - off_f (Eq. 1 with the
 origin shift of Sec. 5).  The kernel does all of it modulo 2^128; the test
-does the same and compares with the direct sums, and checks that A_0..A_4
-stay below 2^64 for segments of at most 128 pixels of 32-bit values.  The
+does the same and compares with the direct sums, and checks that A_0..A_6,
+which the kernel keeps in signed 64-bit words, stay below 2^63 in magnitude
+for segments of at most 64 pixels of 32-bit values (unsigned, or signed
+limbs of magnitude at most 2^31).  The
 batched kernel runs the same cascade over interleaved segments
 (f = g, g + nseg, ...), scaling the Stirling step by (-nseg)^k, modulo 2^64
 when the host's bound says the row power sums fit int64.
@@ -63,11 +65,15 @@ def test_cascade_matches_direct_power_sums():
 
 
 def test_low_cascade_sums_fit_64_bits():
-    # worst case: 128 pixels, every pixel 2^32 - 1
-    top = 2**32 - 1
-    for j in range(5):
-        assert top * comb(128 + j, j + 1) < 2**64
-    assert top * comb(128 + 5, 6) >= 2**64  # A_5 needs the 128-bit path
+    # worst case: 64 pixels, every pixel 2^32 - 1 (or -2^31 for a limb)
+    for top in (2**32 - 1, 2**31):
+        for j in range(7):
+            assert top * comb(64 + j, j + 1) < 2**63
+    assert (2**32 - 1) * comb(64 + 7, 8) >= 2**63  # A_7 needs the 128-bit path
+    # the bound is the largest A_j: every pixel at the maximum
+    for n in (1, 17, 64):
+        A, _ = segment_power_sums([2**32 - 1] * n, 6, 0, 0)
+        assert all(A[j] == (2**32 - 1) * comb(n + j, j + 1) for j in range(7))
 
 
 def test_summed_segments_give_the_row():

@@ -221,6 +221,37 @@ def test_lane_fallback_graph_repeated_calls(dpma):
         assert np.all(np.abs(got - w) <= TOL * mag), (i, name)
 
 
+def test_fallback_inside_a_caller_captured_graph(dpma):
+    """A float32 call captured by the caller (torch.cuda.graph) holds the
+    fallback as a gate kernel and a conditional node.  Replays with contents
+    the quantised pipeline serves and contents that need the fallback must
+    both meet the tolerance."""
+    shape = (12, 30, 32)
+    good = synth.uniform_volume(shape, np.float32, 41, low=0.5, high=1.0)
+    bad = good.copy()
+    bad[5, 6, 7] = 2.0 ** 40
+    want = {n: (oracle.moments(v, 4), oracle.moments(v, 4, absolute=True))
+            for n, v in (("good", good), ("bad", bad))}
+    t = torch.from_numpy(good).cuda()
+    out = torch.empty(dpma.num_moments(4), dtype=torch.float64, device="cuda")
+    ws = torch.empty(dpma.workspace_size(32, 30, 12, dpma.F32, 4), dtype=torch.uint8,
+                     device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        dpma.moments_async(t, 4, out, dpma.F32, workspace=ws)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        dpma.moments_async(t, 4, out, dpma.F32, workspace=ws)
+    for i, name in enumerate(["bad", "good", "bad", "bad", "good"]):
+        t.copy_(torch.from_numpy(good if name == "good" else bad))
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        w, mag = want[name]
+        assert np.all(np.abs(out.cpu().numpy() - w) <= TOL * mag), (i, name)
+
+
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16, np.float32])
 def test_repeated_calls_replay_one_graph(dpma, dtype):
     """From its second call with the same buffers a device-resident pipeline
