@@ -28,10 +28,11 @@ cudaError_t launch_f32(int P, const IntProjectArgs& a, cudaStream_t st);
 
 namespace {
 
-// Grid-stride zeroing with 16-byte stores; block b also takes sampled rows
-// b, b + G, ... of the float volume (row j of the sample is volume row
-// j * rows / nsr, jittered inside its stride) and stores the largest |v|
-// it saw (float bits; NaN propagates) in sample[b].
+// Grid-stride zeroing with 16-byte stores; warp w of the grid also takes
+// sampled rows w, w + W, ... (W warps) of the float volume (row j of the
+// sample is volume row j * rows / nsr, jittered inside its stride), and
+// block b stores the largest |v| its warps saw (float bits; NaN propagates)
+// in sample[b].
 __global__ void clear_sample_kernel(uint4* p, int64_t n16, uint4* p2, int64_t n2,
                                     int* status, int* flags,
                                     const float* vol, int64_t L, int64_t M, int64_t z0,
@@ -43,28 +44,56 @@ __global__ void clear_sample_kernel(uint4* p, int64_t n16, uint4* p2, int64_t n2
     if (status) *status = 0;
     if (flags) *flags = 0;
   }
-  for (int64_t i = gid; i < n16; i += stride) p[i] = make_uint4(0u, 0u, 0u, 0u);
-  for (int64_t i = gid; i < n2; i += stride) p2[i] = make_uint4(0u, 0u, 0u, 0u);
-  if (!sample) return;
+  // one sampled row per warp at a time, its loads (16 per lane) in flight
+  // together; the first row's loads are issued before the zero stores
   const int64_t rows = M * nz;
-  const int64_t step = rows / nsr;  // >= 1
-  float m = 0.f;
-  // one sampled row per warp at a time, so every warp's loads are in flight
-  // together (one memory round trip per row instead of one per block row)
+  const int64_t step = sample ? rows / nsr : 1;  // >= 1
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int lane = threadIdx.x & 31;
-  for (int64_t j = gid >> 5; j < nsr; j += warps) {
+  constexpr int kBatch = 16;
+  auto row_ptr = [&](int64_t j) {
     const int64_t row =
         row_stride > 0 ? j * row_stride : j * rows / nsr + (step > 1 ? (j * 7919) % step : 0);
     const int64_t y = row % M, z = z0 + row / M;
-    const float* src = vol + (z * M + y) * L;
-#pragma unroll 4
-    for (int64_t x = lane; x < L; x += 32) {
-      float d;
-      asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(m), "f"(fabsf(__ldcs(src + x))));
-      m = d;
+    return vol + (z * M + y) * L;
+  };
+  auto absmax = [](float a, float b) {
+    float d;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(fabsf(b)));
+    return d;
+  };
+  float m = 0.f;
+  int64_t j = gid >> 5;
+  float pre[kBatch];
+  const float* first = (sample && j < nsr) ? row_ptr(j) : nullptr;
+  if (first) {
+#pragma unroll
+    for (int k = 0; k < kBatch; ++k) {
+      const int64_t x = lane + 32 * k;
+      pre[k] = x < L ? __ldcs(first + x) : 0.f;
     }
   }
+  for (int64_t i = gid; i < n16; i += stride) p[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int64_t i = gid; i < n2; i += stride) p2[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (!sample) return;
+  // the rest of a row from column c on
+  auto rest = [&](const float* src, int64_t c) {
+    int64_t x = c + lane;
+    for (; x + 32 * (kBatch - 1) < L; x += 32 * kBatch) {
+      float v[kBatch];
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k) v[k] = __ldcs(src + x + 32 * k);
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k) m = absmax(m, v[k]);
+    }
+    for (; x < L; x += 32) m = absmax(m, __ldcs(src + x));
+  };
+  if (first) {
+#pragma unroll
+    for (int k = 0; k < kBatch; ++k) m = absmax(m, pre[k]);
+    rest(first, 32 * kBatch);
+  }
+  for (j += warps; j < nsr; j += warps) rest(row_ptr(j), 0);
   __shared__ float red[32];
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) {
