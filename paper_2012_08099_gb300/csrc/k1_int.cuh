@@ -191,6 +191,39 @@ __device__ __forceinline__ void red_add(uint32_t* p, uint32_t v) {
 __device__ __forceinline__ void red_add_always(uint32_t* p, uint32_t v) {
   asm volatile("red.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// Two neighbouring pixels p[0], p[1] of an unsigned integer image (p 8-byte
+// aligned) in one 64-bit reduction: every partial sum of a pixel stays below
+// its final value, which is below 2^32, so the low word never carries into
+// the high one.
+__device__ __forceinline__ void red_add_pair(uint32_t* p, uint32_t a, uint32_t b) {
+  const unsigned long long v = ((unsigned long long)b << 32) | a;
+  if (v) asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+// v[k] into p[k] for lo <= k < hi, neighbouring pixels paired where p + k is
+// 8-byte aligned (unsigned integer images).
+template <int W>
+__device__ __forceinline__ void red_add_run(uint32_t* p, const uint32_t (&v)[W], int lo, int hi) {
+  auto go = [&](auto par) {
+    constexpr int o = decltype(par)::value;  // 1: p[0] is the high word of a pair
+    auto one = [&](int k) {
+      if (k >= lo && k < hi) red_add(p + k, v[k]);
+    };
+    if constexpr (o == 1) one(0);
+#pragma unroll
+    for (int k = o; k + 1 < W; k += 2) {
+      const bool in_k = k >= lo && k < hi, in_n = k + 1 >= lo && k + 1 < hi;
+      if (in_k && in_n) {
+        red_add_pair(p + k, v[k], v[k + 1]);
+      } else {
+        one(k);
+        one(k + 1);
+      }
+    }
+    if constexpr (((W - o) & 1) == 1) one(W - 1);
+  };
+  if (reinterpret_cast<uintptr_t>(p) & 4) go(std::integral_constant<int, 1>{});
+  else go(std::integral_constant<int, 0>{});
+}
 // Shared-memory reduction (no return value).
 __device__ __forceinline__ void red_shared(uint32_t* p, uint32_t v) {
   asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
@@ -745,19 +778,34 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
       for (int r = 0; r < BYA; ++r) {
         const int y = yt + r;
         if (y >= M) continue;
-#pragma unroll
-        for (int l = 0; l < NL; ++l)
-#pragma unroll
-          for (int k = 0; k < RA; ++k) {
-            if constexpr (H3) {  // slot k
-              const int64_t f = (int64_t)xt + zn + k;
-              if (f < set.F[3]) red_add(pix(3, y, f) + l * lstride, w3[r][l][k]);
-            }
-            if constexpr (H4) {  // slot k + 1
-              const int64_t f = (int64_t)xt + k - zn + c4;
-              if (f >= 0 && f < set.F[4]) red_add(pix(4, y, f) + l * lstride, w4[r][l][k]);
-            }
+        if constexpr (!FL) {
+          // consecutive pixels: paired 64-bit reductions
+          if constexpr (H3) {  // slot k: pixel f3 + k
+            const int64_t f3 = (int64_t)xt + zn;
+            const int64_t hi = set.F[3] - f3;
+            red_add_run<RA>(pix(3, y, f3), w3[r][0], 0, hi < RA ? (int)hi : RA);
           }
+          if constexpr (H4) {  // slot k + 1: pixel f4 + k
+            const int64_t f4 = (int64_t)xt - zn + c4;
+            const int64_t hi = set.F[4] - f4;
+            red_add_run<RA>(pix(4, y, f4), w4[r][0], f4 < 0 ? (int)-f4 : 0,
+                            hi < RA ? (int)hi : RA);
+          }
+        } else {
+#pragma unroll
+          for (int l = 0; l < NL; ++l)
+#pragma unroll
+            for (int k = 0; k < RA; ++k) {
+              if constexpr (H3) {  // slot k
+                const int64_t f = (int64_t)xt + zn + k;
+                if (f < set.F[3]) red_add(pix(3, y, f) + l * lstride, w3[r][l][k]);
+              }
+              if constexpr (H4) {  // slot k + 1
+                const int64_t f = (int64_t)xt + k - zn + c4;
+                if (f >= 0 && f < set.F[4]) red_add(pix(4, y, f) + l * lstride, w4[r][l][k]);
+              }
+            }
+        }
       }
       clear_a();
     }
@@ -961,31 +1009,66 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
       if constexpr (H8) merge_diag(diag8, 8, (s - 1) & 1, z - 2, x0, y0, tid - 32 * NWG);
       // segment end: windows into the images
       const int zn = z;
-#pragma unroll
-      for (int c = 0; c < BXB; ++c) {
-        const int x = xt + c;
-        if (x >= L) continue;
-#pragma unroll
-        for (int l = 0; l < NL; ++l)
+      if constexpr (!FL && BXB == 2) {
+        // the lane's two columns are neighbouring pixels of images 0, 5 and 6:
+        // paired 64-bit reductions
+        const bool in1 = xt + 1 < L;
+        auto pair = [&](uint32_t* q, uint32_t a, uint32_t b) {
+          if (in1 && (reinterpret_cast<uintptr_t>(q) & 7) == 0) {
+            red_add_pair(q, a, b);
+          } else {
+            red_add(q, a);
+            if (in1) red_add(q + 1, b);
+          }
+        };
+        if (xt < L) {
 #pragma unroll
           for (int k = 0; k < RYB; ++k) {
             if (yt + k < M) {
               if constexpr (C::A0SMEM) {
                 const uint32_t* e = reinterpret_cast<const uint32_t*>(a0p[k / 2]);
-                red_add(pix(0, yt + k, x) + l * lstride, e[((k & 1) * BB + c) * NL + l]);
+                pair(pix(0, yt + k, xt), e[(k & 1) * BB], e[(k & 1) * BB + 1]);
               } else {
-                red_add(pix(0, yt + k, x) + l * lstride, a0[k][c][l]);
+                pair(pix(0, yt + k, xt), a0[k][0][0], a0[k][1][0]);
               }
             }
             if constexpr (H5) {  // slot k
               const int64_t sr = (int64_t)yt + zn + k;
-              if (sr < set.S[5]) red_add(pix(5, sr, x) + l * lstride, w5[c][l][k]);
+              if (sr < set.S[5]) pair(pix(5, sr, xt), w5[0][0][k], w5[1][0][k]);
             }
             if constexpr (H6) {  // slot k + 1
               const int64_t sr = (int64_t)yt + k - zn + c6;
-              if (sr >= 0 && sr < set.S[6]) red_add(pix(6, sr, x) + l * lstride, w6[c][l][k]);
+              if (sr >= 0 && sr < set.S[6]) pair(pix(6, sr, xt), w6[0][0][k], w6[1][0][k]);
             }
           }
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < BXB; ++c) {
+          const int x = xt + c;
+          if (x >= L) continue;
+#pragma unroll
+          for (int l = 0; l < NL; ++l)
+#pragma unroll
+            for (int k = 0; k < RYB; ++k) {
+              if (yt + k < M) {
+                if constexpr (C::A0SMEM) {
+                  const uint32_t* e = reinterpret_cast<const uint32_t*>(a0p[k / 2]);
+                  red_add(pix(0, yt + k, x) + l * lstride, e[((k & 1) * BB + c) * NL + l]);
+                } else {
+                  red_add(pix(0, yt + k, x) + l * lstride, a0[k][c][l]);
+                }
+              }
+              if constexpr (H5) {  // slot k
+                const int64_t sr = (int64_t)yt + zn + k;
+                if (sr < set.S[5]) red_add(pix(5, sr, x) + l * lstride, w5[c][l][k]);
+              }
+              if constexpr (H6) {  // slot k + 1
+                const int64_t sr = (int64_t)yt + k - zn + c6;
+                if (sr >= 0 && sr < set.S[6]) red_add(pix(6, sr, x) + l * lstride, w6[c][l][k]);
+              }
+            }
+        }
       }
       clear_b();
       if constexpr (C::A0SMEM) {
