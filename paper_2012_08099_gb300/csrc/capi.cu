@@ -501,7 +501,7 @@ dpma_status enqueue(const void* volume, int64_t L, int64_t M, int64_t N, dpma_dt
     e = launch_clear_sample(images, align_up(w.img_bytes, 16), status, flags,
                             fl && !host_src ? static_cast<const float*>(volume) : nullptr, L, M,
                             0, N, fl && !host_src ? sample : nullptr, &ia_nsample, st, 0,
-                            ws + w.off_m2d, align_up(w.m2d_bytes, 16));
+                            ws + w.off_m2d, align_up(w.m2d_bytes, 16), fl ? kLimbPairBias : 0u);
   }
   if (e != cudaSuccess) return cuda_fail(e, "clear images");
   rec.mark(0, 1);

@@ -154,7 +154,13 @@ cudaError_t launch_project_int(const IntProjectArgs& a, cudaStream_t st);
 cudaError_t launch_clear_sample(void* p, size_t bytes, int* status, int* flags, const float* vol,
                                 int64_t L, int64_t M, int64_t z0, int64_t nz, uint32_t* sample,
                                 int* nsample, cudaStream_t st, int64_t row_stride = 0,
-                                void* p2 = nullptr, size_t bytes2 = 0);
+                                void* p2 = nullptr, size_t bytes2 = 0, uint32_t even_fill = 0);
+// The limb images of a float32 volume start with every pixel at an 8-byte
+// aligned address (the low word of a pixel pair) at kLimbPairBias instead of
+// 0; step 2 removes it.  With it the low word of a pair stays inside
+// [0, 2^32) under any order of additions (|partial sums| < 2^30), so 32-bit
+// reductions and paired 64-bit reductions of sign-extended sums can mix.
+constexpr uint32_t kLimbPairBias = 0x80000000u;
 constexpr int kMaxSample = 2048;  // sample slots
 
 // Step 2 by the discrete Radon route (k2_drt.cu): integer images only.

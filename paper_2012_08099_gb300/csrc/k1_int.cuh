@@ -191,17 +191,22 @@ __device__ __forceinline__ void red_add(uint32_t* p, uint32_t v) {
 __device__ __forceinline__ void red_add_always(uint32_t* p, uint32_t v) {
   asm volatile("red.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-// Two neighbouring pixels p[0], p[1] of an unsigned integer image (p 8-byte
-// aligned) in one 64-bit reduction: every partial sum of a pixel stays below
-// its final value, which is below 2^32, so the low word never carries into
-// the high one.
+// Two neighbouring pixels p[0], p[1] (p 8-byte aligned) in one 64-bit
+// reduction.  Unsigned integer images: every partial sum of a pixel stays
+// below its final value, which is below 2^32, so the low word never carries
+// into the high one.  Limb images (SG): the low word holds kLimbPairBias plus
+// a partial sum of magnitude below 2^30, and `a` is added sign-extended, so
+// again the low word stays inside [0, 2^32) and the high word is exact.
+template <bool SG>
 __device__ __forceinline__ void red_add_pair(uint32_t* p, uint32_t a, uint32_t b) {
-  const unsigned long long v = ((unsigned long long)b << 32) | a;
-  if (v) asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+  const unsigned long long v =
+      ((unsigned long long)b << 32) +
+      (SG ? (unsigned long long)(long long)(int32_t)a : (unsigned long long)a);
+  if (a | b) asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 // v[k] into p[k] for lo <= k < hi, neighbouring pixels paired where p + k is
-// 8-byte aligned (unsigned integer images).
-template <int W>
+// 8-byte aligned.
+template <int W, bool SG>
 __device__ __forceinline__ void red_add_run(uint32_t* p, const uint32_t (&v)[W], int lo, int hi) {
   auto go = [&](auto par) {
     constexpr int o = decltype(par)::value;  // 1: p[0] is the high word of a pair
@@ -213,7 +218,7 @@ __device__ __forceinline__ void red_add_run(uint32_t* p, const uint32_t (&v)[W],
     for (int k = o; k + 1 < W; k += 2) {
       const bool in_k = k >= lo && k < hi, in_n = k + 1 >= lo && k + 1 < hi;
       if (in_k && in_n) {
-        red_add_pair(p + k, v[k], v[k + 1]);
+        red_add_pair<SG>(p + k, v[k], v[k + 1]);
       } else {
         one(k);
         one(k + 1);
@@ -778,33 +783,20 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
       for (int r = 0; r < BYA; ++r) {
         const int y = yt + r;
         if (y >= M) continue;
-        if constexpr (!FL) {
-          // consecutive pixels: paired 64-bit reductions
+        // consecutive pixels: paired 64-bit reductions
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
           if constexpr (H3) {  // slot k: pixel f3 + k
             const int64_t f3 = (int64_t)xt + zn;
             const int64_t hi = set.F[3] - f3;
-            red_add_run<RA>(pix(3, y, f3), w3[r][0], 0, hi < RA ? (int)hi : RA);
+            red_add_run<RA, FL>(pix(3, y, f3) + l * lstride, w3[r][l], 0, hi < RA ? (int)hi : RA);
           }
           if constexpr (H4) {  // slot k + 1: pixel f4 + k
             const int64_t f4 = (int64_t)xt - zn + c4;
             const int64_t hi = set.F[4] - f4;
-            red_add_run<RA>(pix(4, y, f4), w4[r][0], f4 < 0 ? (int)-f4 : 0,
-                            hi < RA ? (int)hi : RA);
+            red_add_run<RA, FL>(pix(4, y, f4) + l * lstride, w4[r][l], f4 < 0 ? (int)-f4 : 0,
+                                hi < RA ? (int)hi : RA);
           }
-        } else {
-#pragma unroll
-          for (int l = 0; l < NL; ++l)
-#pragma unroll
-            for (int k = 0; k < RA; ++k) {
-              if constexpr (H3) {  // slot k
-                const int64_t f = (int64_t)xt + zn + k;
-                if (f < set.F[3]) red_add(pix(3, y, f) + l * lstride, w3[r][l][k]);
-              }
-              if constexpr (H4) {  // slot k + 1
-                const int64_t f = (int64_t)xt + k - zn + c4;
-                if (f >= 0 && f < set.F[4]) red_add(pix(4, y, f) + l * lstride, w4[r][l][k]);
-              }
-            }
         }
       }
       clear_a();
@@ -1015,7 +1007,7 @@ __global__ void __launch_bounds__(Cfg<T, P>::NT, 1)
         const bool in1 = xt + 1 < L;
         auto pair = [&](uint32_t* q, uint32_t a, uint32_t b) {
           if (in1 && (reinterpret_cast<uintptr_t>(q) & 7) == 0) {
-            red_add_pair(q, a, b);
+            red_add_pair<false>(q, a, b);
           } else {
             red_add(q, a);
             if (in1) red_add(q + 1, b);

@@ -37,7 +37,7 @@ __global__ void clear_sample_kernel(uint4* p, int64_t n16, uint4* p2, int64_t n2
                                     int* status, int* flags,
                                     const float* vol, int64_t L, int64_t M, int64_t z0,
                                     int64_t nz, uint32_t* sample, int64_t nsr,
-                                    int64_t row_stride) {
+                                    int64_t row_stride, uint32_t even_fill) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if (gid == 0) {
@@ -73,7 +73,8 @@ __global__ void clear_sample_kernel(uint4* p, int64_t n16, uint4* p2, int64_t n2
       pre[k] = x < L ? __ldcs(first + x) : 0.f;
     }
   }
-  for (int64_t i = gid; i < n16; i += stride) p[i] = make_uint4(0u, 0u, 0u, 0u);
+  // words 0 and 2 of each 16-byte block sit at 8-byte aligned addresses
+  for (int64_t i = gid; i < n16; i += stride) p[i] = make_uint4(even_fill, 0u, even_fill, 0u);
   for (int64_t i = gid; i < n2; i += stride) p2[i] = make_uint4(0u, 0u, 0u, 0u);
   if (!sample) return;
   // the rest of a row from column c on
@@ -152,7 +153,7 @@ cudaError_t launch_project_int(const IntProjectArgs& a, cudaStream_t st) {
 cudaError_t launch_clear_sample(void* p, size_t bytes, int* status, int* flags, const float* vol,
                                 int64_t L, int64_t M, int64_t z0, int64_t nz, uint32_t* sample,
                                 int* nsample, cudaStream_t st, int64_t row_stride, void* p2,
-                                size_t bytes2) {
+                                size_t bytes2, uint32_t even_fill) {
   if ((reinterpret_cast<uintptr_t>(p) & 15) != 0 || (bytes & 15) != 0) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(p2) & 15) != 0 || (bytes2 & 15) != 0) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
@@ -177,7 +178,7 @@ cudaError_t launch_clear_sample(void* p, size_t bytes, int* status, int* flags, 
   if (nsample) *nsample = sample ? (int)blocks : 0;
   k1i::clear_sample_kernel<<<(unsigned)blocks, 256, 0, st>>>(
       static_cast<uint4*>(p), n16, static_cast<uint4*>(p2), p2 ? (int64_t)(bytes2 / 16) : 0,
-      status, flags, vol, L, M, z0, nz, sample, nsr, row_stride);
+      status, flags, vol, L, M, z0, nz, sample, nsr, row_stride, even_fill);
   return cudaGetLastError();
 }
 

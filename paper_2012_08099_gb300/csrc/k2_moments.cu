@@ -95,6 +95,10 @@ __global__ void __launch_bounds__(kUnitThreads) k2_int_cascade_kernel(K2Params p
       static_cast<const uint32_t*>(p.images) + p.set.base[k] + limb * p.set.total_elems;
   const int t = threadIdx.x;
 
+  // limb images: the pixels at 8-byte aligned addresses carry kLimbPairBias
+  auto unbias = [](const uint32_t* at, uint32_t v) -> uint32_t {
+    return (SGN && (reinterpret_cast<uintptr_t>(at) & 4) == 0) ? v ^ kLimbPairBias : v;
+  };
   // the staged pixels, and after the cascades the segments' power sums and
   // the fold partials in the same memory
   struct Sums {
@@ -133,8 +137,8 @@ __global__ void __launch_bounds__(kUnitThreads) k2_int_cascade_kernel(K2Params p
     const int nvec = (int)((plen - head) / 4);
     const int tail0 = head + 4 * nvec;
     auto put = [&](int i, uint32_t v) { sm.stage[i + (i >> lgseg)] = v; };
-    if (t < head) put(t, __ldg(src + t));
-    if (tail0 + t < plen) put(tail0 + t, __ldg(src + tail0 + t));
+    if (t < head) put(t, unbias(src + t, __ldg(src + t)));
+    if (tail0 + t < plen) put(tail0 + t, unbias(src + tail0 + t, __ldg(src + tail0 + t)));
     const uint4* vsrc = reinterpret_cast<const uint4*>(src + head);
     constexpr int kVecPerThread = kSegLenMax / 4;  // nvec <= kUnitThreads * kSegLenMax / 4
     constexpr int kBatch = 8;
@@ -151,9 +155,10 @@ __global__ void __launch_bounds__(kUnitThreads) k2_int_cascade_kernel(K2Params p
         const int vi = t + (j0 + j) * kUnitThreads;
         if (vi < nvec) {
           const int i = head + 4 * vi;
-          put(i, q[j].x);
+          // words 0 and 2 of an aligned 16-byte block are 8-byte aligned
+          put(i, SGN ? q[j].x ^ kLimbPairBias : q[j].x);
           put(i + 1, q[j].y);
-          put(i + 2, q[j].z);
+          put(i + 2, SGN ? q[j].z ^ kLimbPairBias : q[j].z);
           put(i + 3, q[j].w);
         }
       }
@@ -209,7 +214,7 @@ __global__ void __launch_bounds__(kUnitThreads) k2_int_cascade_kernel(K2Params p
         return sm.stage[w + (w >> lgseg)];
       });
     } else {
-      cascade([&](int i) -> uint32_t { return __ldg(row + i); });
+      cascade([&](int i) -> uint32_t { return unbias(row + i, __ldg(row + i)); });
     }
     u128 A[NB];
 #pragma unroll
