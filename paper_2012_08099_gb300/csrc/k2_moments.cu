@@ -50,6 +50,21 @@ __device__ __forceinline__ void atomic_add_u128(i128* dst, u128 v) {
   if (hi + carry) atomicAdd(w + 1, hi + carry);
 }
 
+// The signed product a * b of two 64-bit values, as 128 bits.
+__device__ __forceinline__ u128 mul_s64(int64_t a, int64_t b) {
+  const uint64_t lo = (uint64_t)a * (uint64_t)b;
+  const uint64_t hi = (uint64_t)__mul64hi((long long)a, (long long)b);
+  return ((u128)hi << 64) | lo;
+}
+// x * d modulo 2^128 for a signed 64-bit d (d sign-extended to 128 bits is
+// du - 2^64 for d < 0, du = d modulo 2^64).
+__device__ __forceinline__ u128 mul_u128_s64(u128 x, int64_t d) {
+  const uint64_t xl = (uint64_t)x, xh = (uint64_t)(x >> 64), du = (uint64_t)d;
+  uint64_t hi = __umul64hi(xl, du) + xh * du;
+  if (d < 0) hi -= xl;
+  return ((u128)hi << 64) | (xl * du);
+}
+
 // Integer images by cascaded sums -------------------------------------------
 //
 // For a row segment of n pixels I_0 .. I_{n-1}, running A_0 += I_i,
@@ -90,7 +105,10 @@ __global__ void __launch_bounds__(kUnitThreads) k2_int_cascade_kernel(K2Params p
   const int64_t S = p.set.S[k], F = p.set.F[k];
   const int64_t off_s = p.set.off_s[k], off_f = p.set.off_f[k];
   const int64_t seg = p.seg_len;
-  const int64_t nseg = (F + seg - 1) / seg;
+  const int lgseg = 31 - __clz((int)seg);  // seg is a power of two
+  // segments per row; S * nseg < 2^31 (checked on the host), so the
+  // divisions by nseg below run in 32 bits
+  const uint32_t nseg = (uint32_t)((F + seg - 1) >> lgseg);
   const uint32_t* img =
       static_cast<const uint32_t*>(p.images) + p.set.base[k] + limb * p.set.total_elems;
   const int t = threadIdx.x;
@@ -120,10 +138,9 @@ __global__ void __launch_bounds__(kUnitThreads) k2_int_cascade_kernel(K2Params p
   const int64_t units = S * nseg;
   const int64_t u_first = chunk * kUnitThreads;
   const int64_t u_last = (u_first + kUnitThreads < units ? u_first + kUnitThreads : units) - 1;
-  const int lgseg = 31 - __clz((int)seg);  // seg is a power of two
   int64_t p0, plen;
   {
-    const int64_t s0 = u_first / nseg, sl = u_last / nseg;
+    const int64_t s0 = (uint32_t)u_first / nseg, sl = (uint32_t)u_last / nseg;
     const int64_t gl = u_last - sl * nseg;
     p0 = s0 * F + (u_first - s0 * nseg) * seg;
     plen = sl * F + ((gl + 1) * seg < F ? (gl + 1) * seg : F) - p0;
@@ -173,7 +190,7 @@ __global__ void __launch_bounds__(kUnitThreads) k2_int_cascade_kernel(K2Params p
   for (int b = 0; b < NB; ++b) Fb[b] = 0;
   int64_t cs = 0;
   if (u < units) {
-    const int64_t s = u / nseg, g = u - s * nseg;
+    const int64_t s = (uint32_t)u / nseg, g = u - s * nseg;
     const int64_t fs = g * seg;
     const int n = (int)(F - fs < seg ? F - fs : seg);
     const int o = (int)(s * F + fs - p0);  // the segment's first pixel in the stage
@@ -228,14 +245,16 @@ __global__ void __launch_bounds__(kUnitThreads) k2_int_cascade_kernel(K2Params p
     for (int b = 0; b < NB; ++b) {
       u128 q = 0;
 #pragma unroll
-      for (int j = 0; j <= b; ++j) q += (u128)(i128)c_stirling.v[b][j] * A[j];
+      for (int j = 0; j <= b; ++j)
+        q += j < kCascade64 ? mul_s64((int64_t)a64[j < kCascade64 ? j : 0], c_stirling.v[b][j])
+                            : mul_u128_s64(A[j], c_stirling.v[b][j]);
       Fb[b] = (b & 1) ? (u128)0 - q : q;
     }
-    const u128 D = (u128)(i128)(fs + n - off_f);
+    const int64_t D = fs + n - off_f;
 #pragma unroll
     for (int i = 1; i < NB; ++i)
 #pragma unroll
-      for (int b = NB - 1; b >= i; --b) Fb[b] += D * Fb[b - 1];
+      for (int b = NB - 1; b >= i; --b) Fb[b] += mul_u128_s64(Fb[b - 1], D);
     cs = s - off_s;
   }
   __syncthreads();  // every cascade has read the stage, which Fs overwrites
@@ -255,12 +274,12 @@ __global__ void __launch_bounds__(kUnitThreads) k2_int_cascade_kernel(K2Params p
 #pragma unroll
     for (int a = 0; a < NB; ++a) T[a] = 0;
     auto fold = [&](u128 pw, int64_t srow) {
-      const u128 sv = (u128)(i128)srow;
+
       T[0] += pw;
 #pragma unroll
       for (int a = 1; a < NB; ++a) {
         if (a > K - b) break;
-        pw *= sv;
+        pw = mul_u128_s64(pw, srow);
         T[a] += pw;
       }
     };
@@ -494,6 +513,10 @@ cudaError_t launch_k2(const void* images, const ImageSet& set, int K, bool is_fl
   p.K = K;
   p.npairs = num_2d(K);
   p.seg_len = int_seg_len(set, nl);
+  // the kernels divide segment numbers (S * nseg of them per image) in 32 bits
+  for (int k = 0; k < set.P; ++k)
+    if (set.S[k] * ((set.F[k] + p.seg_len - 1) / p.seg_len) >= ((int64_t)1 << 31))
+      return cudaErrorInvalidValue;
   const int64_t nblk = blocks_of(set, nl, p.blk_base);
   p.partials = partials;
   const unsigned g = (unsigned)nblk;
