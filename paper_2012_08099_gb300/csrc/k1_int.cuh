@@ -187,9 +187,9 @@ __device__ __forceinline__ uint64_t evict_first_policy() {
 // The limb images of a float32 volume are reduced in the L2 with an
 // evict-last hint (H, policy `pol` made once per thread by keep_policy), so
 // that the streaming volume (loaded evict-first) rather than the images
-// leaves the L2 first: their DRAM writes halve (567.2 -> 563.1 MB per launch
-// at 512^3).  Integer images take plain reductions: the hinted form measured
-// slower there.
+// leaves the L2 first: their DRAM write-backs halve (a 512^3 launch moves
+// about 563 instead of 567 MB).  Integer images take plain reductions: the
+// hinted form measured slower there.
 __device__ __forceinline__ uint64_t keep_policy() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
