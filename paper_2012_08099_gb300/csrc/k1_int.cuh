@@ -1216,12 +1216,13 @@ cudaError_t launch(const IntProjectArgs& a, cudaStream_t st) {
     if (dev < 64) { cached_sms[dev] = sms; cached_per_sm[dev] = per_sm; }
   }
   // at least a few z-pairs per CTA so segment ends stay a small overhead:
-  // 4, or 2 for volumes of at most 64 units (measured K1: 64^3 u8 K=3
-  // 16.2 / 12.3 / 10.1 us at 8 / 4 / 2; 128^3 u16 K=6 21.7 / 16.9 / 18.7 us;
-  // 128^3 f32 K=6 22.8 / 17.5 / 18.7 us; 256^3 and larger unchanged)
+  // 4, or 1 for volumes of at most 64 units, where latency rules (measured
+  // K1: 64^3 u8 K=3 16.2 / 12.3 / 10.1 / 9.2 us at 8 / 4 / 2 / 1; 128^3 u16
+  // K=6 21.7 / 16.9 / 18.7 us at 8 / 4 / 2; 128^3 f32 K=6 22.8 / 17.5 / 18.7
+  // us; 256^3 and larger unchanged)
   const int64_t gmax = (int64_t)sms * per_sm;
   const int64_t W = (int64_t)p.nyt * p.nzp;
-  const int64_t min_steps = units <= 64 ? 2 : 4;
+  const int64_t min_steps = units <= 64 ? 1 : 4;
   int64_t grid;
   if (p.nxt <= gmax) {  // nxt CTAs per (band, z-pair) range
     int64_t cpt = gmax / p.nxt;
