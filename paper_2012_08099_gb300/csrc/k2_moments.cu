@@ -78,10 +78,13 @@ __device__ __forceinline__ u128 mul_u128_s64(u128 x, int64_t d) {
 // shift.  Every step is a ring operation, so all of it is exact modulo
 // 2^128, and the 2-D moments, which fit in int128, come out exact.  Per pixel
 // this costs K + 1 additions instead of K products.
-// Pixels per segment at most.  A_j <= max|I| * C(n + j, j + 1), which for n = 64
-// and |I| < 2^32 stays below 2^63 up to j = 6: A_0 .. A_6 run in 64 bits.
+//
+// Pixels per segment at most: |A_j| <= max|I| * C(n + j, j + 1), which for
+// n = 64 and |I| < 2^32 (or limb pixels of magnitude at most 2^31) stays
+// below 2^63 up to j = 6, so A_0 .. A_6 run in signed 64-bit words.
 constexpr int kSegLenMax = 64;
 constexpr int kCascade64 = 7;  // cascade sums kept in 64 bits
+static_assert(kSegLenMax <= 64, "the 64-bit cascade bound holds for segments of at most 64 pixels");
 constexpr int kUnitThreads = 128;  // segments per CTA
 // The segments of one CTA are consecutive in memory (rows follow each other),
 // so the CTA first copies its pixels, at most kUnitThreads * kSegLenMax, into
