@@ -138,3 +138,13 @@ def test_interleaved_segments_modulo_2_64():
             tot = [(a + c) % M64 for a, c in zip(tot, Fs)]
         for b in range(K + 1):
             assert tot[b] == sum((f - off_f) ** b * v for f, v in enumerate(row)) % M64
+
+
+def test_segment_numbers_fit_32_bits_at_the_largest_dimensions():
+    """Step 2 divides segment numbers in 32 bits: even at the largest
+    dimensions (65536 on every axis) and the shortest segments (16 pixels),
+    every image has fewer than 2^31 row segments."""
+    import oracle
+    for k in range(11):
+        S, F, _, _ = oracle.image_geometry(k, 65536, 65536, 65536)
+        assert S * ((F + 15) // 16) < 2**31, k
