@@ -413,13 +413,16 @@ dpma_status dpma_server_submit(dpma_server* server, const dpma_volume_desc* desc
 /*
  * As dpma_server_submit, for a volume named by `key` (0: no key).  The
  * caller promises that one key always names the same volume (dimensions,
- * element type and voxels).  A keyed volume that runs through the
+ * element type and voxels).  A keyed integer volume that runs through the
  * single-volume pipeline leaves its projection images resident in the
  * server's arena; a later request with the same key at an order K no higher
  * than theirs skips the upload and the projection and only takes the image
  * moments and the combine (the image set of order K is a prefix of the set
  * of every larger order, with the same geometry).  Resident images are
  * evicted, least recently used first, when admission needs the memory.
+ * Float32 volumes keep no images: theirs are quantised on a grid of the
+ * volume's own (or redone by the compensated fallback), so a keyed float32
+ * request is computed in full.
  */
 dpma_status dpma_server_submit_keyed(dpma_server* server, const dpma_volume_desc* desc,
                                      uint64_t key, uint64_t* ticket);

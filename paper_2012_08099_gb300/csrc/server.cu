@@ -13,8 +13,10 @@
 // the next requests.  Waiters block on the request's completion.
 //
 // Requests may name their volume with a key.  The images of a keyed
-// single-volume run stay resident in the arena after it completes; a later
-// request for the same key at an order K no higher than the resident one
+// single-volume run of an integer volume stay resident in the arena after it
+// completes (a float32 run's images are limbs on the volume's own
+// quantisation grid, or the fallback's, so float32 keys are not cached); a
+// later request for the same key at an order K no higher than the resident one
 // needs no upload and no projection (the image set of order K is a prefix of
 // every larger order's set, with the same geometry) and runs only the image
 // moments and the combine.  Resident images are evicted, least recently used
@@ -352,7 +354,7 @@ size_t volume_bytes(const Request* r) { return (r->fused || r->src) ? 0 : align2
 
 // A resident entry for the request's key that serves its order (lock held).
 CacheEntry* find_entry(dpma_server* s, const Request* r) {
-  if (!r->key || r->fused) return nullptr;
+  if (!r->key || r->fused || r->d.dtype == DPMA_F32) return nullptr;
   for (CacheEntry* e : s->cache)
     if (!e->stale && e->key == r->key && e->L == r->d.L && e->M == r->d.M && e->N == r->d.N &&
         e->dtype == r->d.dtype && e->K >= r->d.K)
@@ -411,7 +413,8 @@ void retire_group(dpma_server* s, Group* g) {
       }
       r->src = nullptr;
     }
-    if (r->key && !r->fused && !was_hit && r->status == DPMA_OK && r->blk != SIZE_MAX) {
+    if (r->key && !r->fused && r->d.dtype != DPMA_F32 && !was_hit && r->status == DPMA_OK &&
+        r->blk != SIZE_MAX) {
       // keep this run's images resident for later requests with the same key
       for (CacheEntry* e : s->cache)
         if (e->key == r->key && !e->stale) e->stale = true;

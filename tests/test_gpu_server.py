@@ -176,3 +176,18 @@ def test_resident_images_are_evicted_under_pressure(dpma):
         for i, v in enumerate(vols):                     # hits or recomputations: all exact
             t = torch.from_numpy(v.view(np.int16)).cuda()
             assert srv.wait(srv.submit(v, 4, key=100 + i)) == dpma.moments_values(t, 4, dpma.U16)
+
+
+def test_keyed_float_volumes_are_recomputed(dpma):
+    """Float32 images are limbs on the volume's own quantisation grid, so a
+    keyed float32 volume keeps no resident images: a second request with the
+    same key at a lower order is computed in full and meets the tolerance."""
+    vol = synth.mri_like_f32(96, 80, 40, seed=83)
+    with dpma.Server() as srv:
+        for K in (6, 4, 6):
+            got = np.asarray(srv.wait(srv.submit(vol, K, key=77)))
+            want = oracle.moments(vol, K)
+            mag = oracle.moments(vol, K, absolute=True)
+            assert np.all(np.abs(got - want) <= 1e-6 * mag), K
+        st = srv.stats()
+        assert st["cache_hits"] == 0 and st["resident_volumes"] == 0
