@@ -81,3 +81,38 @@ def test_signed_pairs_without_bias_go_wrong():
     lo, hi, _ = run(c, 0, True, rng)
     assert lo == -2
     assert hi != 8
+
+
+def run_ops(W, o, lo, hi):
+    """The reductions the projection kernel's red_add_run issues for window
+    positions k of [lo, hi): ('pair', k) adds k and k + 1 with one 64-bit
+    reduction (p + k 8-byte aligned, i.e. k + o even), ('one', k) a single
+    pixel.  o = 1 when the run's first pixel is the high word of a pair."""
+    ops = []
+    inside = lambda k: lo <= k < hi
+    if o == 1 and inside(0):
+        ops.append(("one", 0))
+    for k in range(o, W - 1, 2):
+        if inside(k) and inside(k + 1):
+            ops.append(("pair", k))
+        else:
+            ops += [("one", j) for j in (k, k + 1) if inside(j)]
+    if (W - o) % 2 == 1 and inside(W - 1):
+        ops.append(("one", W - 1))
+    return ops
+
+
+def test_runs_add_each_position_once_and_pair_only_aligned_words():
+    for W in (4, 8):
+        for o in (0, 1):
+            for lo in range(-2, W + 2):
+                for hi in range(lo, W + 3):
+                    seen = []
+                    for kind, k in run_ops(W, o, lo, hi):
+                        if kind == "pair":
+                            assert (k + o) % 2 == 0 and k + 1 < W
+                            seen += [k, k + 1]
+                        else:
+                            seen.append(k)
+                    want = [k for k in range(W) if lo <= k < hi]
+                    assert sorted(seen) == want, (W, o, lo, hi)
